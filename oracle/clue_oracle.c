@@ -1,0 +1,267 @@
+/*
+ * CLUE oracle: a plain, slow, single-thread CPU restatement of the clustering
+ * of Rovere et al., "CLUE: A Fast Parallel Clustering Algorithm for High
+ * Granularity Calorimeters in High Energy Physics" (arXiv 2001.09761).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the CUDA library is
+ * checked against.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline leg may load it; the library neither includes, links nor calls it,
+ * and it shares no code, header or constant with the library.
+ *
+ * What it computes, step by step in the paper's order:
+ *   1. a fixed square grid per layer (Sec. 2.1, Eqs. 1-2), each bin listing
+ *      its hits in ascending hit index;
+ *   2. local density rho (Eq. 3, Algorithm 1) with the flat kernel chi = 1;
+ *   3. nearest-higher nh and separation delta (Eq. 4, Algorithm 2);
+ *   4. seed / outlier decision and follower registration (Sec. 2.2, Eq. 5,
+ *      first half of Algorithm 3);
+ *   5. cluster expansion by a stack, seed ids passed down the follower lists
+ *      (second half of Algorithm 3).
+ *
+ * Readings where the paper is silent or ambiguous (each is also listed in the
+ * design notes of the repository):
+ *   R1  chi is flat: every j with d_ij < d_c adds w_j, j = i included.
+ *   R2  d_ij is Euclidean in (x, y) on the same layer only, compared squared in
+ *       fp32: dx = x_j - x_i, dy = y_j - y_i, d2 = dx*dx + dy*dy, every
+ *       operation rounded to nearest with no fused multiply-add (this file is
+ *       built with -ffp-contract=off).  Thresholds are squared once in fp32.
+ *       The reported delta is sqrtf(d2).
+ *   R3  every comparison is strict, as printed: d < d_c, d < d_m, rho_j > rho_i,
+ *       seed iff rho > rho_c and delta > delta_c, outlier iff rho < rho_c and
+ *       delta > delta_o.
+ *   R4  rho is summed in fp32, starting from +0, over N_dc(i) in ascending j.
+ *   R5  among nearest-higher candidates at equal d2 the smallest j wins.
+ *   R7  a hit that is neither seed nor outlier and has nh = -1 (possible only
+ *       when rho == rho_c) is not registered anywhere and stays noise.
+ *   R8  cluster ids are 0..k-1 in ascending seed index over the whole event
+ *       (all layers), as the k++ of Algorithm 3 gives.
+ *   R9  noise gets cluster id -1.
+ *   R10 hits outside the grid extent fall into the edge bins; the search
+ *       window is widened by a tiny margin so that floating-point rounding can
+ *       never drop a true neighbour (the exact d2 test decides membership, so
+ *       the result does not depend on the bin size).
+ *   R11 delta = +inf when nh = -1.
+ *
+ * Input errors (n < 0, a NaN or infinite coordinate or weight, a layer outside
+ * [0, n_layers), invalid parameters) return a negative code and leave the
+ * outputs unspecified.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_ARG -1
+#define ORACLE_ERR_INPUT -2
+#define ORACLE_ERR_OOM -3
+
+/* Squared distance of R2 (fp32, no contraction). */
+static float sq_dist(float xi, float yi, float xj, float yj)
+{
+    float dx = xj - xi;
+    float dy = yj - yi;
+    float ax = dx * dx;
+    float ay = dy * dy;
+    return ax + ay;
+}
+
+/* Monotone bin index of coordinate v on an axis starting at lo with bins of
+ * width s; out-of-range values land in the edge bins (R10). */
+static int64_t axis_bin(double v, double lo, double s, int64_t nb)
+{
+    double t = floor((v - lo) / s);
+    if (!(t > 0.0))
+        t = 0.0;
+    if (t > (double)(nb - 1))
+        t = (double)(nb - 1);
+    return (int64_t)t;
+}
+
+/* Half-width of the search window of radius d around coordinate v: d plus a
+ * margin far larger than any rounding of the fp32 distance test (R10). */
+static double window_half(double d, double v)
+{
+    return d * (1.0 + 1e-6) + fabs(v) * 1e-9;
+}
+
+static int cmp_int64(const void *a, const void *b)
+{
+    int64_t p = *(const int64_t *)a, q = *(const int64_t *)b;
+    return (p > q) - (p < q);
+}
+
+static int param_ok(float d)
+{
+    return isfinite(d) && d >= 0.0f && isfinite(d * d);
+}
+
+/*
+ * Cluster one event of n hits.  Outputs (all length n, caller-owned):
+ *   rho, delta (sqrtf of the squared separation, +inf when nh = -1),
+ *   delta2 (the squared separation), nh (nearest-higher index or -1),
+ *   is_seed (0/1), is_outlier (0/1), cluster_id (0..k-1 or -1).
+ * Any output pointer may be NULL.  Returns ORACLE_OK or a negative code.
+ */
+int oracle_clue(int64_t n, const float *x, const float *y, const int32_t *layer,
+                const float *w, int32_t n_layers, float x_min, float x_max,
+                float y_min, float y_max, float dc, float rhoc, float delta_c,
+                float delta_o, float *rho_out, float *delta_out, float *delta2_out,
+                int32_t *nh_out, uint8_t *is_seed_out, uint8_t *is_outlier_out,
+                int32_t *cluster_id_out, int64_t *n_seeds_out)
+{
+    if (n < 0 || n_layers <= 0 || !(dc > 0.0f) || !param_ok(dc) || !param_ok(delta_c) ||
+        !param_ok(delta_o) || !isfinite(rhoc) || !isfinite(x_min) || !isfinite(x_max) ||
+        !isfinite(y_min) || !isfinite(y_max) || !(x_max > x_min) || !(y_max > y_min))
+        return ORACLE_ERR_ARG;
+    if (n > 0 && (!x || !y || !layer || !w))
+        return ORACLE_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!isfinite(x[i]) || !isfinite(y[i]) || !isfinite(w[i]) || layer[i] < 0 ||
+            layer[i] >= n_layers)
+            return ORACLE_ERR_INPUT;
+    }
+    if (n_seeds_out)
+        *n_seeds_out = 0;
+    if (n == 0)
+        return ORACLE_OK;
+
+    /* Sec. 2.2: d_m = max(delta_o, delta_c); thresholds squared once in fp32. */
+    const float dm = delta_o > delta_c ? delta_o : delta_c;
+    const float dc2 = dc * dc;
+    const float dm2 = dm * dm;
+    const float delta_c2 = delta_c * delta_c;
+    const float delta_o2 = delta_o * delta_o;
+
+    /* Step 1: fixed grid per layer, bin size max(d_c, d_m) (any size works). */
+    const double s = (double)(dm > dc ? dm : dc);
+    const int64_t nbx = (int64_t)ceil(((double)x_max - x_min) / s) > 0
+                            ? (int64_t)ceil(((double)x_max - x_min) / s) : 1;
+    const int64_t nby = (int64_t)ceil(((double)y_max - y_min) / s) > 0
+                            ? (int64_t)ceil(((double)y_max - y_min) / s) : 1;
+    const int64_t n_cells = (int64_t)n_layers * nbx * nby;
+    if (nbx > (1 << 20) || nby > (1 << 20) || n_cells > ((int64_t)1 << 31))
+        return ORACLE_ERR_ARG;
+
+    int64_t *head = malloc(sizeof(int64_t) * (size_t)n_cells);
+    int64_t *next = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *buf = malloc(sizeof(int64_t) * (size_t)n);
+    float *rho = malloc(sizeof(float) * (size_t)n);
+    float *d2v = malloc(sizeof(float) * (size_t)n);
+    int64_t *nh = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *cid = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *fol_head = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *fol_next = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *stack = malloc(sizeof(int64_t) * (size_t)n);
+    uint8_t *seed = malloc((size_t)n);
+    uint8_t *outl = malloc((size_t)n);
+    if (!head || !next || !buf || !rho || !d2v || !nh || !cid || !fol_head || !fol_next ||
+        !stack || !seed || !outl) {
+        free(head); free(next); free(buf); free(rho); free(d2v); free(nh); free(cid);
+        free(fol_head); free(fol_next); free(stack); free(seed); free(outl);
+        return ORACLE_ERR_OOM;
+    }
+    for (int64_t c = 0; c < n_cells; ++c)
+        head[c] = -1;
+    /* Register each hit in its bin; pushing in descending index order leaves
+     * every bin list in ascending index order. */
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int64_t bx = axis_bin(x[i], x_min, s, nbx);
+        int64_t by = axis_bin(y[i], y_min, s, nby);
+        int64_t c = ((int64_t)layer[i] * nby + by) * nbx + bx;
+        next[i] = head[c];
+        head[c] = i;
+    }
+
+    /* Step 2 (Eq. 3, Algorithm 1): rho_i over Omega_dc(i), summed in
+     * ascending j (R4). */
+    for (int64_t i = 0; i < n; ++i) {
+        double hx = window_half(dc, x[i]), hy = window_half(dc, y[i]);
+        int64_t bx0 = axis_bin((double)x[i] - hx, x_min, s, nbx);
+        int64_t bx1 = axis_bin((double)x[i] + hx, x_min, s, nbx);
+        int64_t by0 = axis_bin((double)y[i] - hy, y_min, s, nby);
+        int64_t by1 = axis_bin((double)y[i] + hy, y_min, s, nby);
+        int64_t m = 0;
+        for (int64_t by = by0; by <= by1; ++by)
+            for (int64_t bx = bx0; bx <= bx1; ++bx)
+                for (int64_t j = head[((int64_t)layer[i] * nby + by) * nbx + bx]; j >= 0;
+                     j = next[j])
+                    if (sq_dist(x[i], y[i], x[j], y[j]) < dc2)
+                        buf[m++] = j;
+        qsort(buf, (size_t)m, sizeof(int64_t), cmp_int64);
+        float r = 0.0f;
+        for (int64_t k = 0; k < m; ++k)
+            r += w[buf[k]];
+        rho[i] = r;
+    }
+
+    /* Step 3 (Eq. 4, Algorithm 2): nearest-higher within d_m, ties by the
+     * smaller index (R5); none gives nh = -1, delta = +inf (R11). */
+    for (int64_t i = 0; i < n; ++i) {
+        double hx = window_half(dm, x[i]), hy = window_half(dm, y[i]);
+        int64_t bx0 = axis_bin((double)x[i] - hx, x_min, s, nbx);
+        int64_t bx1 = axis_bin((double)x[i] + hx, x_min, s, nbx);
+        int64_t by0 = axis_bin((double)y[i] - hy, y_min, s, nby);
+        int64_t by1 = axis_bin((double)y[i] + hy, y_min, s, nby);
+        float best = INFINITY;
+        int64_t arg = -1;
+        for (int64_t by = by0; by <= by1; ++by)
+            for (int64_t bx = bx0; bx <= bx1; ++bx)
+                for (int64_t j = head[((int64_t)layer[i] * nby + by) * nbx + bx]; j >= 0;
+                     j = next[j]) {
+                    float d2 = sq_dist(x[i], y[i], x[j], y[j]);
+                    if (d2 < dm2 && rho[j] > rho[i]) {
+                        if (d2 < best || (d2 == best && j < arg)) {
+                            best = d2;
+                            arg = j;
+                        }
+                    }
+                }
+        d2v[i] = best;
+        nh[i] = arg;
+    }
+
+    /* Step 4 (Sec. 2.2, Eq. 5, Algorithm 3): seeds get ids in index order,
+     * outliers are left out, everything else registers with its nh (R7). */
+    int64_t k = 0, top = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        fol_head[i] = -1;
+        cid[i] = -1;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        seed[i] = (rho[i] > rhoc) && (d2v[i] > delta_c2);
+        outl[i] = (rho[i] < rhoc) && (d2v[i] > delta_o2);
+        if (seed[i]) {
+            cid[i] = k++;
+            stack[top++] = i;
+        } else if (!outl[i] && nh[i] >= 0) {
+            fol_next[i] = fol_head[nh[i]];
+            fol_head[nh[i]] = i;
+        }
+    }
+
+    /* Step 5 (Algorithm 3): pass the ids down the follower lists. */
+    while (top > 0) {
+        int64_t i = stack[--top];
+        for (int64_t j = fol_head[i]; j >= 0; j = fol_next[j]) {
+            cid[j] = cid[i];
+            stack[top++] = j;
+        }
+    }
+
+    for (int64_t i = 0; i < n; ++i) {
+        if (rho_out) rho_out[i] = rho[i];
+        if (delta2_out) delta2_out[i] = d2v[i];
+        if (delta_out) delta_out[i] = sqrtf(d2v[i]);
+        if (nh_out) nh_out[i] = (int32_t)nh[i];
+        if (is_seed_out) is_seed_out[i] = seed[i];
+        if (is_outlier_out) is_outlier_out[i] = outl[i];
+        if (cluster_id_out) cluster_id_out[i] = (int32_t)cid[i];
+    }
+    if (n_seeds_out)
+        *n_seeds_out = k;
+
+    free(head); free(next); free(buf); free(rho); free(d2v); free(nh); free(cid);
+    free(fol_head); free(fol_next); free(stack); free(seed); free(outl);
+    return ORACLE_OK;
+}
