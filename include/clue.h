@@ -1,0 +1,196 @@
+/*
+ * clue.h -- C ABI of the GB300 CLUE library (libclue.so).
+ *
+ * CLUE (Rovere et al., arXiv 2001.09761) clusters the hits of a calorimeter
+ * event layer by layer: a fixed square grid per layer (Sec. 2.1, Eqs. 1-2),
+ * the local density rho (Eq. 3, Algorithm 1), the nearest-higher nh and
+ * separation delta (Eq. 4, Algorithm 2), the seed / outlier decision with
+ * follower lists (Sec. 2.2, Eq. 5, Algorithm 3) and the expansion of cluster
+ * ids down the follower chains (Algorithm 3).  The input is one structure of
+ * arrays over all layers of an event (Sec. 3).
+ *
+ * Arithmetic contract (identical on every call, every bin size and every
+ * launch shape, so results are reproducible bit for bit):
+ *   - distances are compared squared in fp32: dx = x_j - x_i, dy = y_j - y_i,
+ *     d2 = dx*dx + dy*dy, each operation rounded to nearest, no fused
+ *     multiply-add; thresholds are squared once in fp32;
+ *   - chi is flat: rho_i is the fp32 sum, from +0 in ascending hit index j, of
+ *     w_j over all hits j of i's layer with d2 < d_c^2 (j = i included);
+ *   - nh_i is the hit j of i's layer with rho_j > rho_i and d2 < d_m^2,
+ *     d_m = max(delta_c, delta_o), of smallest d2, the smaller index on a tie;
+ *     -1 (and delta = +inf) when there is none;
+ *   - seed iff rho > rho_c and delta^2 > delta_c^2; outlier iff rho < rho_c and
+ *     delta^2 > delta_o^2; every other hit with nh != -1 follows its nh;
+ *   - cluster ids are numbered 0..k-1 per event in ascending seed index and
+ *     passed from each seed to all its descendants; outliers, their
+ *     descendants, and non-seed hits with no nearest-higher get -1.
+ *
+ * Memory and threading: every array argument of clue_run / clue_run_batch is
+ * a DEVICE pointer (e.g. a torch CUDA tensor's data pointer) on the context's
+ * device, owned by the caller, and must stay valid until clue_sync returns.
+ * Work is queued on the context's stream and returns before it finishes.
+ * The context owns a grow-only scratch arena (allocated once per size, as the
+ * paper's Sec. 4.2 allocates once before the event loop).  A context is used
+ * by one host thread at a time.
+ *
+ * Errors: every call returns CLUE_OK (0) or a CLUE_ERR_* code; nothing aborts
+ * and nothing traps on the device.  Errors in the inputs (a NaN or infinite
+ * coordinate or energy, a layer outside [0, max_layers)) are detected on the
+ * device and returned by the next clue_sync; the outputs of that run are then
+ * unspecified.
+ */
+#ifndef CLUE_H
+#define CLUE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CLUE_OK 0
+#define CLUE_ERR_ARG 1      /* invalid argument (null pointer, bad size or parameter) */
+#define CLUE_ERR_INPUT 2    /* invalid input values found on the device */
+#define CLUE_ERR_OOM 3      /* device or pinned host allocation failed */
+#define CLUE_ERR_CUDA 4     /* a CUDA runtime call failed (see clue_last_message) */
+#define CLUE_ERR_TIMEOUT 5  /* a bounded device-side wait gave up */
+#define CLUE_ERR_STATE 6    /* call not valid in the context's current state */
+
+typedef struct clue_ctx clue_ctx;
+
+/* Context options.  Fill with clue_default_opts, then override. */
+typedef struct clue_opts {
+    int32_t device;      /* CUDA device ordinal */
+    float x_min, x_max;  /* grid extent (cm); hits outside fall into edge bins */
+    float y_min, y_max;
+    int32_t max_layers;  /* layer ids must lie in [0, max_layers) */
+    float bin_size;      /* grid bin size (cm); 0 = from the tuning table */
+    int32_t block_size;  /* threads per block of the density kernels; 0 = tuned */
+    int32_t use_graphs;  /* 1 = capture a repeated call into a CUDA graph and replay it */
+    void *stream;        /* cudaStream_t to queue work on; NULL = context-owned stream */
+} clue_opts;
+
+/* Defaults: device 0, extent [-250, 250]^2, 128 layers, tuned bin/block,
+ * graphs on, own stream. */
+void clue_default_opts(clue_opts *opts);
+
+/* Create a context on opts->device.  *out receives the context.
+ * Errors: CLUE_ERR_ARG (null, extent not finite/increasing, max_layers < 1,
+ * bin_size < 0), CLUE_ERR_CUDA. */
+int clue_create(clue_ctx **out, const clue_opts *opts);
+
+/* Release the context and everything it owns (waits for its work first). */
+void clue_destroy(clue_ctx *ctx);
+
+/* Queue later work on another stream (cudaStream_t; NULL = the context's own). */
+int clue_set_stream(clue_ctx *ctx, void *stream);
+
+/*
+ * Cluster one event of n hits (Sec. 2, Algorithms 1-3).
+ *   x, y      float32[n]  hit coordinates (cm)
+ *   layer     int32[n]    layer id in [0, max_layers)
+ *   energy    float32[n]  hit weight w (Eq. 3)
+ *   n         0 <= n <= 2^31 - 2 (n = 0 is a no-op)
+ *   dc        cut-off distance d_c > 0 (Eq. 2-3)
+ *   rhoc      density threshold rho_c (finite)
+ *   delta_c   seed separation delta_c >= 0 (Sec. 2.2)
+ *   delta_o   outlier separation delta_o >= 0 (Sec. 2.2)
+ *   cluster_id int32[n] out: cluster id 0..k-1, or -1 for noise
+ *   is_seed    uint8[n] out: 1 for seeds, else 0
+ * All arrays are device pointers; see the header comment for ownership.
+ * Errors: CLUE_ERR_ARG, CLUE_ERR_OOM, CLUE_ERR_CUDA (immediately);
+ * CLUE_ERR_INPUT, CLUE_ERR_TIMEOUT (from the next clue_sync).
+ */
+int clue_run(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+             const float *energy, int64_t n, float dc, float rhoc, float delta_c,
+             float delta_o, int32_t *cluster_id, uint8_t *is_seed);
+
+/*
+ * Cluster a batch of independent events in one pass (one launch per stage for
+ * the whole batch).  Event e owns hits [offsets[e], offsets[e+1]) of the
+ * concatenated device arrays x, y, layer, energy, cluster_id, is_seed.
+ *   offsets   HOST int64[n_events + 1], offsets[0] = 0, non-decreasing,
+ *             offsets[n_events] <= 2^31 - 2
+ *   n_events  >= 0
+ * Cluster ids are numbered per event (each event starts at 0).
+ * The same parameters apply to every event.  Errors as clue_run.
+ */
+int clue_run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+                   const float *energy, const int64_t *offsets, int32_t n_events, float dc,
+                   float rhoc, float delta_c, float delta_o, int32_t *cluster_id,
+                   uint8_t *is_seed);
+
+/*
+ * As clue_run_batch, but every array (x, y, layer, energy, cluster_id,
+ * is_seed, offsets) is a HOST pointer (pinned memory is fastest).  The call
+ * copies the inputs to context-owned device buffers, clusters, copies the
+ * results back and returns when they are in host memory (it synchronises).
+ * Errors: as clue_run_batch, including CLUE_ERR_INPUT / CLUE_ERR_TIMEOUT.
+ */
+int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+                        const float *energy, const int64_t *offsets, int32_t n_events,
+                        float dc, float rhoc, float delta_c, float delta_o,
+                        int32_t *cluster_id, uint8_t *is_seed);
+
+/* Wait for the context's queued work; returns the first deferred error
+ * (CLUE_ERR_INPUT, CLUE_ERR_TIMEOUT, CLUE_ERR_CUDA) or CLUE_OK, and clears it. */
+int clue_sync(clue_ctx *ctx);
+
+/*
+ * Copy per-hit intermediates of the last run into caller DEVICE arrays of the
+ * last run's total hit count (any may be NULL): rho (Eq. 3), delta (sqrt of
+ * the fp32 squared separation, +inf when none, Eq. 4) and nh (Eq. 4, index
+ * within the hit's event, -1 when none).  Queued on the context's stream.
+ * Errors: CLUE_ERR_STATE before any run.
+ */
+int clue_get_intermediates(clue_ctx *ctx, float *rho, float *delta, int32_t *nh);
+
+/*
+ * Tune the grid bin size and the density kernels' block size per event-size
+ * class on the given device batch (same arguments as clue_run_batch; results
+ * of the trial runs are written to cluster_id / is_seed).  Every candidate
+ * gives bit-identical results; only speed differs.  `reps` timed repetitions
+ * per candidate (>= 1).  Synchronises.  Errors as clue_run_batch.
+ */
+int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+                  const float *energy, const int64_t *offsets, int32_t n_events, float dc,
+                  float rhoc, float delta_c, float delta_o, int32_t *cluster_id,
+                  uint8_t *is_seed, int32_t reps);
+
+/* Write the tuning table as text "class_lo class_hi bin_scale block\n..." into
+ * buf (capacity cap bytes, NUL-terminated); returns the length needed, or a
+ * negative CLUE_ERR_* code. */
+int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap);
+
+/* Replace the tuning table from text in the format of clue_get_tuning.
+ * Errors: CLUE_ERR_ARG on malformed text. */
+int clue_set_tuning(clue_ctx *ctx, const char *text);
+
+/* Per-stage timing: when on (1), the next runs record a CUDA event between
+ * pipeline stages.  clue_stage_times waits for the last run and writes up to
+ * `cap` stage durations in ms (order: grid fill, rho, nh/delta, decide and
+ * follower lists, expand) and their names (comma-separated, into names if not
+ * NULL, capacity names_cap); returns the number of stages or a negative code. */
+int clue_set_profiling(clue_ctx *ctx, int32_t on);
+int clue_stage_times(clue_ctx *ctx, float *ms, int32_t cap, char *names, int64_t names_cap);
+
+/* Number of kernels the last run launched (for launch accounting). */
+int32_t clue_last_launch_count(clue_ctx *ctx);
+
+/* Device bytes the context's scratch arena holds now. */
+int64_t clue_scratch_bytes(clue_ctx *ctx);
+
+/* Human-readable text of a CLUE_ERR_* code. */
+const char *clue_strerror(int code);
+
+/* Text of the last CUDA error the context saw ("" if none). */
+const char *clue_last_message(clue_ctx *ctx);
+
+/* Library version string. */
+const char *clue_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLUE_H */

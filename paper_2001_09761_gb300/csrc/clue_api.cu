@@ -1,0 +1,843 @@
+// Host side of libclue: the C ABI declared in include/clue.h.
+//
+// A context owns a stream, a grow-only scratch arena (one allocation per size,
+// reused by every later call, as the paper allocates once before its event
+// loop), pinned staging for the per-call plan tables, a small cache of CUDA
+// graphs for calls that repeat, and the tuning table (bin size per event-size
+// class and block size of the density kernels).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cinttypes>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "clue.h"
+#include "clue_internal.h"
+
+using namespace clue;
+
+namespace {
+
+constexpr int NCLASS = 5;
+constexpr int64_t CLASS_EDGE[NCLASS + 1] = {0, 32768, 100000, 316228, 1000000, INT64_MAX};
+constexpr int NSTAGE_EVENTS = 6;
+constexpr int NSTAGING = 4;
+constexpr size_t GRAPH_CACHE_MAX = 16;
+constexpr int64_t MAX_HITS = 2147483646LL;
+
+int class_of(int64_t n) {
+    for (int k = 0; k < NCLASS; ++k)
+        if (n < CLASS_EDGE[k + 1]) return k;
+    return NCLASS - 1;
+}
+
+struct GraphEntry {
+    uint64_t sig = 0;
+    cudaGraphExec_t exec = nullptr;
+    void *dtables = nullptr;
+    Buffers buf{};
+    LaunchCfg cfg{};
+    int launches = 0;
+    uint64_t last_use = 0;
+};
+
+struct Staging {
+    void *host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+};
+
+struct Plan {
+    std::vector<EventDesc> ev;
+    std::vector<Tile> tiles;
+    int64_t N = 0, C = 0;
+};
+
+uint64_t fnv(uint64_t h, const void *p, size_t n) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct clue_ctx {
+    clue_opts opts{};
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    char *arena = nullptr;
+    size_t arena_cap = 0;
+    void *dtables = nullptr;
+    size_t dtables_cap = 0;
+    Staging staging[NSTAGING];
+    int staging_next = 0;
+    Ctrl *d_ctrl = nullptr;
+    Ctrl *h_ctrl = nullptr;
+    float bin_scale[NCLASS];
+    int block_density = 256;
+    bool profiling = false;
+    bool prof_recorded = false;
+    cudaEvent_t pev[NSTAGE_EVENTS] = {};
+    Buffers last{};
+    LaunchCfg last_cfg{};
+    bool have_last = false;
+    int last_launches = 0;
+    std::vector<GraphEntry> graphs;
+    std::unordered_map<uint64_t, int> seen;
+    uint64_t tick = 0;
+    char *hio = nullptr;
+    size_t hio_cap = 0;
+    std::string msg;
+};
+
+namespace {
+
+int cuda_fail(clue_ctx *c, cudaError_t e, const char *what) {
+    if (c) {
+        c->msg = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return e == cudaErrorMemoryAllocation ? CLUE_ERR_OOM : CLUE_ERR_CUDA;
+}
+
+#define CK(call)                                                    \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);    \
+    } while (0)
+
+bool param_ok(float d) { return std::isfinite(d) && d >= 0.0f && d <= 1e18f; }
+
+int check_params(float dc, float rhoc, float delta_c, float delta_o) {
+    if (!(dc >= 1e-18f) || !param_ok(dc) || !param_ok(delta_c) || !param_ok(delta_o) ||
+        !std::isfinite(rhoc))
+        return CLUE_ERR_ARG;
+    return CLUE_OK;
+}
+
+Params make_params(const clue_ctx *ctx, float dc, float rhoc, float delta_c, float delta_o) {
+    Params p;
+    const float dm = delta_o > delta_c ? delta_o : delta_c;
+    p.dc2 = dc * dc;
+    p.dm2 = dm * dm;
+    p.dcs2 = delta_c * delta_c;
+    p.dos2 = delta_o * delta_o;
+    p.rhoc = rhoc;
+    const float grow = 1.0f + 0x1p-12f;
+    p.rwin_rho = dc * grow;
+    p.rwin_nh = dm * grow;
+    p.L = ctx->opts.max_layers;
+    return p;
+}
+
+float bin_for(const clue_ctx *ctx, int64_t n, float dc) {
+    float s = ctx->opts.bin_size > 0.0f ? ctx->opts.bin_size
+                                        : ctx->bin_scale[class_of(n)] * 2.0f * dc * 1.001f;
+    return s < dc ? dc : s;
+}
+
+int build_plan(clue_ctx *ctx, const int64_t *offsets, int32_t E, float dc, Plan &plan) {
+    const clue_opts &o = ctx->opts;
+    const double wx = (double)o.x_max - o.x_min, wy = (double)o.y_max - o.y_min;
+    plan.ev.resize(E);
+    plan.tiles.clear();
+    int64_t C = 0;
+    for (int32_t e = 0; e < E; ++e) {
+        const int64_t n = offsets[e + 1] - offsets[e];
+        double s = bin_for(ctx, n, dc);
+        int64_t nbx, nby;
+        // Keep the grid O(n): at most 16 cells per hit plus 64 per layer.
+        const double cap = 16.0 * (double)n + 64.0 * o.max_layers;
+        for (int it = 0;; ++it) {
+            nbx = std::max<int64_t>(1, (int64_t)std::ceil(wx / s));
+            nby = std::max<int64_t>(1, (int64_t)std::ceil(wy / s));
+            const double cells = (double)nbx * nby * o.max_layers;
+            if ((cells <= cap && nbx <= (1 << 20) && nby <= (1 << 20)) || it > 60) break;
+            s *= std::max(1.05, std::sqrt(cells / cap));
+        }
+        if (n == 0) nbx = nby = 1;
+        EventDesc &d = plan.ev[e];
+        std::memset(&d, 0, sizeof(d));
+        d.hit_off = offsets[e];
+        d.cell_off = C;
+        d.n = (int32_t)n;
+        d.nbx = (int32_t)nbx;
+        d.nby = (int32_t)nby;
+        d.xmin = o.x_min;
+        d.ymin = o.y_min;
+        d.inv_s = (float)(1.0 / s);
+        C += (int64_t)o.max_layers * nbx * nby;
+        if (C > MAX_HITS) {
+            ctx->msg = "grid too large: raise bin_size or shrink the extent";
+            return CLUE_ERR_ARG;
+        }
+        for (int64_t t = 0; t < n; t += TILE)
+            plan.tiles.push_back(Tile{(int32_t)(offsets[e] + t),
+                                      (int32_t)std::min<int64_t>(TILE, n - t), e, 0});
+    }
+    plan.N = offsets[E];
+    plan.C = C;
+    return CLUE_OK;
+}
+
+// Carve the scratch arrays of a run out of the arena; grows the arena
+// (after draining the stream) when it is too small.  With `dry` set only the
+// size is computed.
+size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
+    size_t off = 0;
+    char *base = ctx->arena;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = dry ? nullptr : (void *)(base + off);
+        off += align_up(bytes);
+        return p;
+    };
+    const size_t n = (size_t)N, c = (size_t)C;
+    b.key = (int32_t *)take(n * 4);
+    b.count = (int32_t *)take(c * 4);
+    b.cell_start = (int32_t *)take((c + 1) * 4);
+    b.perm = (int32_t *)take(n * 4);
+    b.tmp = (int32_t *)take(n * 4);
+    b.big = (int32_t *)take((n / SMALL_SEGMENT + 1) * 4);
+    b.ids_s = (int32_t *)take(n * 4);
+    b.xs = (float *)take(n * 4);
+    b.ys = (float *)take(n * 4);
+    b.ws = (float *)take(n * 4);
+    b.lay_s = (int32_t *)take(n * 4);
+    b.rho_s = (float *)take(n * 4);
+    b.rho = (float *)take(n * 4);
+    b.delta2 = (float *)take(n * 4);
+    b.nh = (int32_t *)take(n * 4);
+    b.flags = (uint8_t *)take(n);
+    b.fcount = (int32_t *)take(n * 4);
+    b.hs = (unsigned long long *)take((n + 1) * 8);
+    b.fol = (int32_t *)take(n * 4);
+    b.seed_list = (int32_t *)take(n * 4);
+    const int64_t parts = std::max(scan_partials_needed(N), scan_partials_needed(C)) + 1;
+    b.scan_partials = take((size_t)parts * 8);
+    b.scan_partials_cap = parts;
+    return off;
+}
+
+void drop_graphs(clue_ctx *ctx) {
+    for (auto &g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.dtables) cudaFree(g.dtables);
+    }
+    ctx->graphs.clear();
+    ctx->seen.clear();
+}
+
+int ensure_arena(clue_ctx *ctx, size_t need) {
+    if (need <= ctx->arena_cap) return CLUE_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);
+    if (ctx->arena) cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    ctx->arena_cap = 0;
+    const size_t cap = need + need / 8 + (1 << 20);
+    CK(cudaMalloc(&ctx->arena, cap));
+    ctx->arena_cap = cap;
+    return CLUE_OK;
+}
+
+size_t tables_bytes(const Plan &plan) {
+    return align_up(plan.ev.size() * sizeof(EventDesc)) + plan.tiles.size() * sizeof(Tile);
+}
+
+void fill_tables(const Plan &plan, char *dst) {
+    std::memcpy(dst, plan.ev.data(), plan.ev.size() * sizeof(EventDesc));
+    std::memcpy(dst + align_up(plan.ev.size() * sizeof(EventDesc)), plan.tiles.data(),
+                plan.tiles.size() * sizeof(Tile));
+}
+
+void point_tables(Buffers &b, const Plan &plan, void *dtables) {
+    b.events = (const EventDesc *)dtables;
+    b.tiles = (const Tile *)((char *)dtables + align_up(plan.ev.size() * sizeof(EventDesc)));
+    b.ntiles = (int32_t)plan.tiles.size();
+    b.nevents = (int32_t)plan.ev.size();
+    b.N = plan.N;
+    b.C = plan.C;
+}
+
+// Upload the plan tables through pinned staging (stream-ordered, so the host
+// can build the next plan while this one is still queued).
+int upload_tables_async(clue_ctx *ctx, const Plan &plan) {
+    const size_t bytes = tables_bytes(plan);
+    if (bytes > ctx->dtables_cap) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->dtables) cudaFree(ctx->dtables);
+        ctx->dtables = nullptr;
+        ctx->dtables_cap = 0;
+        const size_t cap = bytes + bytes / 4 + 4096;
+        CK(cudaMalloc(&ctx->dtables, cap));
+        ctx->dtables_cap = cap;
+    }
+    Staging &st = ctx->staging[ctx->staging_next];
+    ctx->staging_next = (ctx->staging_next + 1) % NSTAGING;
+    CK(cudaEventSynchronize(st.done));
+    if (bytes > st.cap) {
+        if (st.host) cudaFreeHost(st.host);
+        st.host = nullptr;
+        st.cap = 0;
+        const size_t cap = bytes + bytes / 4 + 4096;
+        CK(cudaMallocHost(&st.host, cap));
+        st.cap = cap;
+    }
+    fill_tables(plan, (char *)st.host);
+    CK(cudaMemcpyAsync(ctx->dtables, st.host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaEventRecord(st.done, ctx->stream));
+    return CLUE_OK;
+}
+
+LaunchCfg make_cfg(const clue_ctx *ctx) {
+    LaunchCfg c;
+    c.block_fill = 256;
+    c.block_density = ctx->opts.block_size > 0 ? ctx->opts.block_size : ctx->block_density;
+    c.grid_cap = ctx->num_sms * 8;
+    return c;
+}
+
+// Queue the whole pipeline (S1 grid fill .. S5 expansion) on ctx->stream.
+int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &cfg,
+            int *launches) {
+    cudaStream_t s = ctx->stream;
+    int nl = 0;
+    const bool prof = ctx->profiling;
+    // Inside a stream capture a plain event record is only a dependency edge;
+    // an external record becomes a graph node that stamps the event on replay.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cap));
+    const unsigned rec_flags =
+        cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+#define REC(i) CK(cudaEventRecordWithFlags(ctx->pev[i], s, rec_flags))
+    CK(cudaMemsetAsync(&b.ctrl->overflow, 0, 2 * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
+    if (prof) REC(0);
+    CK(launch_fill_count(b, p, cfg, s));
+    CK(launch_scan_cells(b, cfg, s, &nl));
+    CK(launch_fill_scatter(b, cfg, s));
+    CK(launch_fill_canon(b, cfg, s));
+    CK(launch_fill_big(b, cfg, s));
+    nl += 4;
+    if (prof) REC(1);
+    CK(launch_rho(b, p, cfg, s));
+    if (prof) REC(2);
+    CK(launch_nh(b, p, cfg, s));
+    if (prof) REC(3);
+    CK(launch_decide(b, p, cfg, s));
+    CK(launch_scan_hits(b, cfg, s, &nl));
+    CK(launch_link(b, cfg, s));
+    if (prof) REC(4);
+    CK(launch_expand(b, cfg, s));
+    CK(launch_complete(b, cfg, s));
+    if (prof) REC(5);
+    nl += 6;
+#undef REC
+    *launches = nl;
+    return CLUE_OK;
+}
+
+uint64_t signature(const clue_ctx *ctx, const Plan &plan, const Buffers &b, const Params &p,
+                   const LaunchCfg &cfg) {
+    uint64_t h = 1469598103934665603ULL;
+    h = fnv(h, plan.ev.data(), plan.ev.size() * sizeof(EventDesc));
+    const void *ptrs[6] = {b.x, b.y, b.layer, b.w, b.cid, b.is_seed};
+    h = fnv(h, ptrs, sizeof(ptrs));
+    h = fnv(h, &p, sizeof(p));
+    h = fnv(h, &cfg, sizeof(cfg));
+    const int prof = ctx->profiling;
+    h = fnv(h, &prof, sizeof(prof));
+    h = fnv(h, &ctx->arena, sizeof(ctx->arena));
+    return h;
+}
+
+int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+              const float *energy, const int64_t *offsets, int32_t E, float dc, float rhoc,
+              float delta_c, float delta_o, int32_t *cid, uint8_t *is_seed, bool allow_graph) {
+    if (!ctx || E < 0 || (E > 0 && !offsets)) return CLUE_ERR_ARG;
+    int rc = check_params(dc, rhoc, delta_c, delta_o);
+    if (rc) return rc;
+    if (E == 0) return CLUE_OK;
+    if (offsets[0] != 0) return CLUE_ERR_ARG;
+    for (int32_t e = 0; e < E; ++e)
+        if (offsets[e + 1] < offsets[e]) return CLUE_ERR_ARG;
+    const int64_t N = offsets[E];
+    if (N > MAX_HITS) return CLUE_ERR_ARG;
+    if (N == 0) return CLUE_OK;
+    if (!x || !y || !layer || !energy || !cid || !is_seed) return CLUE_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+
+    Plan plan;
+    rc = build_plan(ctx, offsets, E, dc, plan);
+    if (rc) return rc;
+    Buffers b{};
+    const size_t need = carve(ctx, b, plan.N, plan.C, true);
+    rc = ensure_arena(ctx, need);
+    if (rc) return rc;
+    carve(ctx, b, plan.N, plan.C, false);
+    b.x = x;
+    b.y = y;
+    b.w = energy;
+    b.layer = layer;
+    b.cid = cid;
+    b.is_seed = is_seed;
+    b.ctrl = ctx->d_ctrl;
+    const Params p = make_params(ctx, dc, rhoc, delta_c, delta_o);
+    const LaunchCfg cfg = make_cfg(ctx);
+
+    const bool graphs = allow_graph && ctx->opts.use_graphs && ctx->stream != nullptr;
+    if (graphs) {
+        const uint64_t sig = signature(ctx, plan, b, p, cfg);
+        for (auto &g : ctx->graphs)
+            if (g.sig == sig) {
+                CK(cudaGraphLaunch(g.exec, ctx->stream));
+                g.last_use = ++ctx->tick;
+                ctx->last = g.buf;
+                ctx->last_cfg = g.cfg;
+                ctx->have_last = true;
+                ctx->last_launches = g.launches;
+                ctx->prof_recorded = ctx->profiling;
+                return CLUE_OK;
+            }
+        if (ctx->seen.size() > 4096) ctx->seen.clear();  // one-off batches never repeat
+        if (ctx->seen[sig]++ >= 1) {  // second sighting: capture
+            if (ctx->graphs.size() >= GRAPH_CACHE_MAX) {
+                CK(cudaStreamSynchronize(ctx->stream));
+                auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                           [](const GraphEntry &a, const GraphEntry &c) {
+                                               return a.last_use < c.last_use;
+                                           });
+                cudaGraphExecDestroy(it->exec);
+                cudaFree(it->dtables);
+                ctx->graphs.erase(it);
+            }
+            GraphEntry g;
+            g.sig = sig;
+            const size_t tb = tables_bytes(plan);
+            std::vector<char> host(tb);
+            fill_tables(plan, host.data());
+            CK(cudaMalloc(&g.dtables, tb));
+            cudaError_t e = cudaMemcpy(g.dtables, host.data(), tb, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(g.dtables);
+                return cuda_fail(ctx, e, "cudaMemcpy(tables)");
+            }
+            g.buf = b;
+            point_tables(g.buf, plan, g.dtables);
+            g.cfg = cfg;
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                int launches = 0;
+                const int erc = enqueue(ctx, g.buf, p, cfg, &launches);
+                g.launches = launches;
+                e = cudaStreamEndCapture(ctx->stream, &graph);
+                if (erc != CLUE_OK && e == cudaSuccess) e = cudaErrorUnknown;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(g.dtables);
+                return cuda_fail(ctx, e, "graph capture");
+            }
+            CK(cudaGraphLaunch(g.exec, ctx->stream));
+            g.last_use = ++ctx->tick;
+            ctx->graphs.push_back(g);
+            ctx->last = g.buf;
+            ctx->last_cfg = cfg;
+            ctx->have_last = true;
+            ctx->last_launches = g.launches;
+            ctx->prof_recorded = ctx->profiling;
+            return CLUE_OK;
+        }
+    }
+    rc = upload_tables_async(ctx, plan);
+    if (rc) return rc;
+    point_tables(b, plan, ctx->dtables);
+    int launches = 0;
+    rc = enqueue(ctx, b, p, cfg, &launches);
+    if (rc) return rc;
+    ctx->last = b;
+    ctx->last_cfg = cfg;
+    ctx->have_last = true;
+    ctx->last_launches = launches;
+    ctx->prof_recorded = ctx->profiling;
+    return CLUE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void clue_default_opts(clue_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->device = 0;
+    o->x_min = -250.0f;
+    o->x_max = 250.0f;
+    o->y_min = -250.0f;
+    o->y_max = 250.0f;
+    o->max_layers = 128;
+    o->bin_size = 0.0f;
+    o->block_size = 0;
+    o->use_graphs = 1;
+    o->stream = nullptr;
+}
+
+int clue_create(clue_ctx **out, const clue_opts *opts) {
+    if (!out || !opts) return CLUE_ERR_ARG;
+    *out = nullptr;
+    const clue_opts &o = *opts;
+    if (!std::isfinite(o.x_min) || !std::isfinite(o.x_max) || !std::isfinite(o.y_min) ||
+        !std::isfinite(o.y_max) || !(o.x_max > o.x_min) || !(o.y_max > o.y_min) ||
+        o.max_layers < 1 || !(o.bin_size >= 0.0f) || !std::isfinite(o.bin_size) ||
+        o.block_size < 0 || o.block_size > 512 || (o.block_size % 32) != 0)
+        return CLUE_ERR_ARG;
+    clue_ctx *ctx = new (std::nothrow) clue_ctx();
+    if (!ctx) return CLUE_ERR_OOM;
+    ctx->opts = o;
+    ctx->device = o.device;
+    const float defaults[NCLASS] = {3.0f, 2.0f, 1.5f, 1.0f, 1.0f};
+    for (int k = 0; k < NCLASS; ++k) ctx->bin_scale[k] = defaults[k];
+    auto fail = [&](cudaError_t e, const char *what) {
+        int rc = cuda_fail(ctx, e, what);
+        clue_destroy(ctx);
+        return rc;
+    };
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) return fail(e, "cudaSetDevice");
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
+    if (e != cudaSuccess) return fail(e, "cudaDeviceGetAttribute");
+    if (o.stream) {
+        ctx->stream = (cudaStream_t)o.stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(e, "cudaStreamCreate");
+        ctx->stream = ctx->own;
+    }
+    e = cudaMalloc(&ctx->d_ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) return fail(e, "cudaMalloc(ctrl)");
+    e = cudaMemset(ctx->d_ctrl, 0, sizeof(Ctrl));
+    if (e != cudaSuccess) return fail(e, "cudaMemset(ctrl)");
+    e = cudaMallocHost(&ctx->h_ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) return fail(e, "cudaMallocHost(ctrl)");
+    for (int i = 0; i < NSTAGING; ++i) {
+        e = cudaEventCreateWithFlags(&ctx->staging[i].done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(e, "cudaEventCreate");
+    }
+    for (int i = 0; i < NSTAGE_EVENTS; ++i) {
+        e = cudaEventCreate(&ctx->pev[i]);
+        if (e != cudaSuccess) return fail(e, "cudaEventCreate");
+    }
+    *out = ctx;
+    return CLUE_OK;
+}
+
+void clue_destroy(clue_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->dtables) cudaFree(ctx->dtables);
+    if (ctx->hio) cudaFree(ctx->hio);
+    if (ctx->d_ctrl) cudaFree(ctx->d_ctrl);
+    if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+    for (auto &s : ctx->staging) {
+        if (s.host) cudaFreeHost(s.host);
+        if (s.done) cudaEventDestroy(s.done);
+    }
+    for (auto &ev : ctx->pev)
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->own) cudaStreamDestroy(ctx->own);
+    delete ctx;
+}
+
+int clue_set_stream(clue_ctx *ctx, void *stream) {
+    if (!ctx) return CLUE_ERR_ARG;
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own;
+    if (!s) return CLUE_ERR_ARG;  // context was created on a caller stream and has no own
+    if (s == ctx->stream) return CLUE_OK;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));  // keep the shared scratch ordered
+    ctx->stream = s;
+    drop_graphs(ctx);
+    return CLUE_OK;
+}
+
+int clue_run(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+             const float *energy, int64_t n, float dc, float rhoc, float delta_c,
+             float delta_o, int32_t *cluster_id, uint8_t *is_seed) {
+    if (!ctx || n < 0 || n > MAX_HITS) return CLUE_ERR_ARG;
+    const int64_t offs[2] = {0, n};
+    return run_batch(ctx, x, y, layer, energy, offs, 1, dc, rhoc, delta_c, delta_o, cluster_id,
+                     is_seed, true);
+}
+
+int clue_run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+                   const float *energy, const int64_t *offsets, int32_t n_events, float dc,
+                   float rhoc, float delta_c, float delta_o, int32_t *cluster_id,
+                   uint8_t *is_seed) {
+    return run_batch(ctx, x, y, layer, energy, offsets, n_events, dc, rhoc, delta_c, delta_o,
+                     cluster_id, is_seed, true);
+}
+
+int clue_sync(clue_ctx *ctx) {
+    if (!ctx) return CLUE_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpyAsync(ctx->h_ctrl, ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const unsigned err = ctx->h_ctrl->err;
+    if (err) {
+        CK(cudaMemsetAsync(&ctx->d_ctrl->err, 0, sizeof(unsigned), ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (err & ERRBIT_INPUT) return CLUE_ERR_INPUT;
+        return CLUE_ERR_TIMEOUT;
+    }
+    return CLUE_OK;
+}
+
+int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+                        const float *energy, const int64_t *offsets, int32_t n_events,
+                        float dc, float rhoc, float delta_c, float delta_o,
+                        int32_t *cluster_id, uint8_t *is_seed) {
+    if (!ctx || n_events < 0 || (n_events > 0 && !offsets)) return CLUE_ERR_ARG;
+    if (n_events == 0) return CLUE_OK;
+    const int64_t N = offsets[n_events];
+    if (N < 0 || N > MAX_HITS) return CLUE_ERR_ARG;
+    if (N == 0) return check_params(dc, rhoc, delta_c, delta_o);
+    if (!x || !y || !layer || !energy || !cluster_id || !is_seed) return CLUE_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const size_t n = (size_t)N;
+    const size_t need = 5 * align_up(n * 4) + align_up(n);
+    if (need > ctx->hio_cap) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        drop_graphs(ctx);
+        if (ctx->hio) cudaFree(ctx->hio);
+        ctx->hio = nullptr;
+        ctx->hio_cap = 0;
+        const size_t cap = need + need / 8 + (1 << 20);
+        CK(cudaMalloc(&ctx->hio, cap));
+        ctx->hio_cap = cap;
+    }
+    char *p = ctx->hio;
+    float *dx = (float *)p;
+    float *dy = (float *)(p + align_up(n * 4));
+    int32_t *dl = (int32_t *)(p + 2 * align_up(n * 4));
+    float *de = (float *)(p + 3 * align_up(n * 4));
+    int32_t *dc_out = (int32_t *)(p + 4 * align_up(n * 4));
+    uint8_t *ds = (uint8_t *)(p + 5 * align_up(n * 4));
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(dx, x, n * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dy, y, n * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dl, layer, n * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(de, energy, n * 4, cudaMemcpyHostToDevice, s));
+    int rc = run_batch(ctx, dx, dy, dl, de, offsets, n_events, dc, rhoc, delta_c, delta_o, dc_out,
+                       ds, true);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(cluster_id, dc_out, n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(is_seed, ds, n, cudaMemcpyDeviceToHost, s));
+    return clue_sync(ctx);
+}
+
+int clue_get_intermediates(clue_ctx *ctx, float *rho, float *delta, int32_t *nh) {
+    if (!ctx) return CLUE_ERR_ARG;
+    if (!ctx->have_last) return CLUE_ERR_STATE;
+    CK(cudaSetDevice(ctx->device));
+    // The last run's tables may live in a graph entry or in the shared table
+    // buffer; both stay valid until the next run or arena growth.
+    CK(launch_export(ctx->last, ctx->last_cfg, rho, delta, nh, ctx->stream));
+    return CLUE_OK;
+}
+
+int clue_set_profiling(clue_ctx *ctx, int32_t on) {
+    if (!ctx) return CLUE_ERR_ARG;
+    ctx->profiling = on != 0;
+    return CLUE_OK;
+}
+
+int clue_stage_times(clue_ctx *ctx, float *ms, int32_t cap, char *names, int64_t names_cap) {
+    if (!ctx || (cap > 0 && !ms)) return -CLUE_ERR_ARG;
+    static const char kNames[] = "grid_fill,rho,nh_delta,decide_followers,expand";
+    if (names && names_cap > 0) {
+        std::strncpy(names, kNames, (size_t)names_cap - 1);
+        names[names_cap - 1] = 0;
+    }
+    if (!ctx->prof_recorded) return -CLUE_ERR_STATE;
+    cudaError_t e = cudaEventSynchronize(ctx->pev[NSTAGE_EVENTS - 1]);
+    if (e != cudaSuccess) return -cuda_fail(ctx, e, "cudaEventSynchronize");
+    const int n = NSTAGE_EVENTS - 1;
+    for (int i = 0; i < n && i < cap; ++i) {
+        e = cudaEventElapsedTime(&ms[i], ctx->pev[i], ctx->pev[i + 1]);
+        if (e != cudaSuccess) return -cuda_fail(ctx, e, "cudaEventElapsedTime");
+    }
+    return n;
+}
+
+int32_t clue_last_launch_count(clue_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+int64_t clue_scratch_bytes(clue_ctx *ctx) {
+    return ctx ? (int64_t)(ctx->arena_cap + ctx->dtables_cap + ctx->hio_cap) : 0;
+}
+
+int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+                  const float *energy, const int64_t *offsets, int32_t n_events, float dc,
+                  float rhoc, float delta_c, float delta_o, int32_t *cluster_id,
+                  uint8_t *is_seed, int32_t reps) {
+    if (!ctx || reps < 1 || n_events < 1 || !offsets) return CLUE_ERR_ARG;
+    int rc = check_params(dc, rhoc, delta_c, delta_o);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    bool present[NCLASS] = {};
+    for (int32_t e = 0; e < n_events; ++e) present[class_of(offsets[e + 1] - offsets[e])] = true;
+    cudaEvent_t t0, t1;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;
+    auto time_run = [&](float *out_ms) -> int {
+        // one untimed run (plans, arena growth), then `reps` timed ones
+        int r = run_batch(ctx, x, y, layer, energy, offsets, n_events, dc, rhoc, delta_c,
+                          delta_o, cluster_id, is_seed, false);
+        if (r) return r;
+        cudaError_t e = cudaEventRecord(t0, ctx->stream);
+        for (int i = 0; i < reps && r == CLUE_OK && e == cudaSuccess; ++i)
+            r = run_batch(ctx, x, y, layer, energy, offsets, n_events, dc, rhoc, delta_c,
+                          delta_o, cluster_id, is_seed, false);
+        if (r) return r;
+        if (e == cudaSuccess) e = cudaEventRecord(t1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(out_ms, t0, t1);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune timing");
+        return clue_sync(ctx);
+    };
+    const float scales[] = {1.0f, 1.5f, 2.0f, 3.0f, 4.0f};
+    const int blocks[] = {128, 256, 512};
+    const float user_bin = ctx->opts.bin_size;
+    const int user_block = ctx->opts.block_size;
+    ctx->opts.bin_size = 0.0f;
+    ctx->opts.block_size = 0;
+    for (int k = 0; k < NCLASS && rc == CLUE_OK; ++k) {
+        if (!present[k]) continue;
+        float best = 1e30f, best_s = ctx->bin_scale[k];
+        for (float s : scales) {
+            ctx->bin_scale[k] = s;
+            float ms = 0;
+            rc = time_run(&ms);
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                best_s = s;
+            }
+        }
+        ctx->bin_scale[k] = best_s;
+    }
+    if (rc == CLUE_OK) {
+        float best = 1e30f;
+        int best_b = ctx->block_density;
+        for (int bsz : blocks) {
+            ctx->block_density = bsz;
+            float ms = 0;
+            rc = time_run(&ms);
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                best_b = bsz;
+            }
+        }
+        ctx->block_density = best_b;
+    }
+    ctx->opts.bin_size = user_bin;
+    ctx->opts.block_size = user_block;
+    ctx->profiling = prof;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    drop_graphs(ctx);
+    return rc;
+}
+
+int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap) {
+    if (!ctx) return -CLUE_ERR_ARG;
+    std::string s = "# clue tuning v1: class <lo> <hi> <bin_scale>; block <threads>\n";
+    char line[160];
+    for (int k = 0; k < NCLASS; ++k) {
+        std::snprintf(line, sizeof(line), "class %" PRId64 " %" PRId64 " %.4f\n", CLASS_EDGE[k],
+                      CLASS_EDGE[k + 1], (double)ctx->bin_scale[k]);
+        s += line;
+    }
+    std::snprintf(line, sizeof(line), "block %d\n", ctx->block_density);
+    s += line;
+    if (buf && cap > 0) {
+        std::strncpy(buf, s.c_str(), (size_t)cap - 1);
+        buf[cap - 1] = 0;
+    }
+    return (int64_t)s.size() + 1;
+}
+
+int clue_set_tuning(clue_ctx *ctx, const char *text) {
+    if (!ctx || !text) return CLUE_ERR_ARG;
+    float scale[NCLASS];
+    for (int k = 0; k < NCLASS; ++k) scale[k] = ctx->bin_scale[k];
+    int block = ctx->block_density;
+    const char *p = text;
+    while (*p) {
+        const char *eol = std::strchr(p, '\n');
+        std::string line(p, eol ? (size_t)(eol - p) : std::strlen(p));
+        p = eol ? eol + 1 : p + line.size();
+        if (line.empty() || line[0] == '#') continue;
+        long long lo, hi;
+        float sc;
+        int bl;
+        char tail;
+        if (std::sscanf(line.c_str(), "class %lld %lld %f %c", &lo, &hi, &sc, &tail) == 3) {
+            int k = -1;
+            for (int i = 0; i < NCLASS; ++i)
+                if (CLASS_EDGE[i] == lo && CLASS_EDGE[i + 1] == hi) k = i;
+            if (k < 0 || !(sc >= 0.25f && sc <= 64.0f)) return CLUE_ERR_ARG;
+            scale[k] = sc;
+        } else if (std::sscanf(line.c_str(), "block %d %c", &bl, &tail) == 1) {
+            if (bl < 32 || bl > 512 || bl % 32) return CLUE_ERR_ARG;
+            block = bl;
+        } else {
+            return CLUE_ERR_ARG;
+        }
+    }
+    for (int k = 0; k < NCLASS; ++k) ctx->bin_scale[k] = scale[k];
+    ctx->block_density = block;
+    drop_graphs(ctx);
+    return CLUE_OK;
+}
+
+const char *clue_strerror(int code) {
+    switch (code) {
+        case CLUE_OK: return "ok";
+        case CLUE_ERR_ARG: return "invalid argument";
+        case CLUE_ERR_INPUT: return "invalid input values (NaN/Inf coordinate or energy, or layer out of range)";
+        case CLUE_ERR_OOM: return "out of memory";
+        case CLUE_ERR_CUDA: return "CUDA error";
+        case CLUE_ERR_TIMEOUT: return "bounded device wait gave up";
+        case CLUE_ERR_STATE: return "invalid state for this call";
+        default: return "unknown error";
+    }
+}
+
+const char *clue_last_message(clue_ctx *ctx) { return ctx ? ctx->msg.c_str() : ""; }
+
+const char *clue_version(void) { return "clue-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal declarations shared by the CUDA translation units of libclue.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace clue {
+
+// Hits are processed in tiles of TILE consecutive indices that never straddle
+// an event; tile t covers [tiles[t].start, tiles[t].start + tiles[t].len).
+constexpr int TILE = 1024;
+
+// A cell segment longer than this is sorted by one CTA (radix) instead of by
+// per-slot ranking.
+constexpr int SMALL_SEGMENT = 128;
+
+// Per-warp queue capacity of the frontier expansion (node ids).
+constexpr int EXPAND_QCAP = 512;
+
+// cluster id of a follower whose id has not been passed down yet.
+constexpr int32_t PENDING = -2;
+
+// flag bits of a hit after the decision step
+constexpr uint8_t F_SEED = 1, F_OUTLIER = 2, F_FOLLOWER = 4;
+
+// Error bits raised on the device (ctrl->err).
+constexpr unsigned ERRBIT_INPUT = 1u, ERRBIT_TIMEOUT = 2u;
+
+struct EventDesc {
+    int64_t hit_off;   // first hit of the event in the batch
+    int64_t cell_off;  // first grid cell of the event in the batch
+    int32_t n;         // hits
+    int32_t nbx, nby;  // bins per layer along x and y
+    float xmin, ymin;  // grid origin
+    float inv_s;       // 1 / bin size
+    int32_t pad[2];
+};
+static_assert(sizeof(EventDesc) == 48, "EventDesc layout");
+
+struct Tile {
+    int32_t start;  // first hit (batch index)
+    int32_t len;    // hits in the tile (1..TILE)
+    int32_t event;  // event index
+    int32_t pad;
+};
+
+// Device control block: zeroed at the start of every run.
+struct Ctrl {
+    unsigned err;        // ERRBIT_* raised by any kernel
+    unsigned overflow;   // an expansion queue overflowed
+    int32_t nbig;        // cell segments queued for the CTA sorter
+    int32_t pad;
+};
+
+// Runtime parameters of one run (all events share them).
+struct Params {
+    float dc2;       // d_c^2 (fp32)
+    float dm2;       // d_m^2, d_m = max(delta_c, delta_o)
+    float dcs2;      // delta_c^2
+    float dos2;      // delta_o^2
+    float rhoc;
+    float rwin_rho;  // d_c * (1 + 2^-12): window half-width before the |v| margin
+    float rwin_nh;   // d_m * (1 + 2^-12)
+    int32_t L;       // layers per event (grid planes)
+};
+
+// Device pointers of one run, carved from the scratch arena.
+struct Buffers {
+    // inputs / outputs (caller-owned)
+    const float *x, *y, *w;
+    const int32_t *layer;
+    int32_t *cid;
+    uint8_t *is_seed;
+    // plan tables
+    const EventDesc *events;
+    const Tile *tiles;
+    int32_t ntiles;
+    int32_t nevents;
+    int64_t N;      // total hits
+    int64_t C;      // total cells
+    // grid
+    int32_t *key;        // [N] local cell of hit
+    int32_t *count;      // [C] hits per cell (zeroed per run)
+    int32_t *cell_start; // [C + 1]
+    int32_t *perm;       // [N] hit ids grouped by cell, unordered within a cell
+    int32_t *tmp;        // [N] scratch for the CTA sorter
+    int32_t *big;        // [N / SMALL_SEGMENT + 1] cells queued for the CTA sorter
+    int32_t *ids_s;      // [N] hit ids sorted by (cell, id)
+    float *xs, *ys, *ws; // [N] coordinates and weights in sorted order
+    int32_t *lay_s;      // [N] layer in sorted order
+    // density
+    float *rho_s;        // [N] rho in sorted order
+    float *rho;          // [N] rho by hit
+    float *delta2;       // [N] squared separation by hit
+    int32_t *nh;         // [N] nearest-higher (batch index) or -1
+    // decision / expansion
+    uint8_t *flags;      // [N]
+    int32_t *fcount;     // [N] followers per hit (zeroed in the fill step)
+    unsigned long long *hs;  // [N + 1] exclusive scan of (seed << 32 | followers)
+    int32_t *fol;        // [N] follower lists (CSR by nh)
+    int32_t *seed_list;  // [N] seeds by global seed rank
+    // scan scratch
+    void *scan_partials; // [nblocks + 1] block sums
+    int64_t scan_partials_cap;
+    Ctrl *ctrl;
+};
+
+// Launch configuration chosen per run.
+struct LaunchCfg {
+    int block_fill;     // threads per block: grid fill / decide kernels
+    int block_density;  // threads per block: rho / nh kernels
+    int grid_cap;       // persistent grid size (multiple of the SM count)
+};
+
+// ---- launchers (each enqueues its kernel(s) on `s`; return cudaError_t) ----
+cudaError_t launch_fill_count(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_scan_cells(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
+cudaError_t launch_fill_scatter(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_fill_big(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_decide(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
+cudaError_t launch_link(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_complete(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_export(const Buffers &b, const LaunchCfg &c, float *rho, float *delta,
+                          int32_t *nh, cudaStream_t s);
+
+// Scan scratch needed for n elements (in elements of 8 bytes).
+int64_t scan_partials_needed(int64_t n);
+
+}  // namespace clue

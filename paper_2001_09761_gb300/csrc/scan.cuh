@@ -1,0 +1,103 @@
+// Device-wide exclusive prefix sum in three launches (tile reduce, scan of
+// the tile sums in one CTA, tile scan plus offset).  No CTA ever waits on
+// another, so nothing can spin.  Used for the grid's cell offsets and for the
+// seed ranks / follower-list offsets of the decision step.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace clue {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int64_t SCAN_TILE = (int64_t)SCAN_THREADS * SCAN_ITEMS;
+
+// Inclusive scan over the CTA (blockDim.x a multiple of 32, <= 1024).
+// `ws` is shared scratch of >= 32 elements; *total gets the CTA sum.
+template <typename T>
+__device__ __forceinline__ T block_incl_scan(T v, T *ws, T *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T incl = warp_incl_scan(v);
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T s = lane < nw ? ws[lane] : T(0);
+        s = warp_incl_scan(s);
+        if (lane < nw) ws[lane] = s;
+    }
+    __syncthreads();
+    const T add = warp > 0 ? ws[warp - 1] : T(0);
+    *total = ws[nw - 1];
+    __syncthreads();
+    return incl + add;
+}
+
+template <typename T, typename Load>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Load ld, int64_t n, T *partials,
+                                                              int64_t ntiles) {
+    __shared__ T ws[32];
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t base = t * SCAN_TILE;
+        T sum = 0;
+#pragma unroll 4
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const int64_t idx = base + (int64_t)i * SCAN_THREADS + threadIdx.x;
+            if (idx < n) sum += ld(idx);
+        }
+        T total;
+        block_incl_scan(sum, ws, &total);
+        if (threadIdx.x == 0) partials[t] = total;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_mid(T *partials, int64_t ntiles, T *out, int64_t n) {
+    __shared__ T ws[32];
+    T carry = 0;
+    for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const T v = i < ntiles ? partials[i] : T(0);
+        T total;
+        const T incl = block_incl_scan(v, ws, &total);
+        if (i < ntiles) partials[i] = carry + incl - v;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        partials[ntiles] = carry;
+        out[n] = carry;
+    }
+}
+
+template <typename T, typename Load>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(Load ld, int64_t n, const T *partials,
+                                                            T *out, int64_t ntiles) {
+    __shared__ T ws[32];
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t base = t * SCAN_TILE;
+        T carry = partials[t];
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const int64_t idx = base + (int64_t)i * SCAN_THREADS + threadIdx.x;
+            const T v = idx < n ? ld(idx) : T(0);
+            T total;
+            const T incl = block_incl_scan(v, ws, &total);
+            if (idx < n) out[idx] = carry + incl - v;
+            carry += total;
+        }
+    }
+}
+
+// Exclusive scan of ld(0..n-1) into out[0..n-1], out[n] = total.
+// `partials` must hold scan_partials_needed(n) elements of T.
+template <typename T, typename Load>
+cudaError_t exclusive_scan(Load ld, int64_t n, T *out, T *partials, int grid_cap, cudaStream_t s,
+                           int *launches) {
+    const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    const int grid = (int)(ntiles < grid_cap ? (ntiles > 0 ? ntiles : 1) : grid_cap);
+    k_scan_reduce<T, Load><<<grid, SCAN_THREADS, 0, s>>>(ld, n, partials, ntiles);
+    k_scan_mid<T><<<1, 1024, 0, s>>>(partials, ntiles, out, n);
+    k_scan_down<T, Load><<<grid, SCAN_THREADS, 0, s>>>(ld, n, partials, out, ntiles);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace clue

@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerance: 0.  Cluster ids, seed flags and nearest-higher indices are integer
+outputs and must match exactly; rho and delta follow a fixed fp32 operation
+order on both sides (ascending-index summation, unfused distance) and are
+compared bit for bit.
+"""
+from __future__ import annotations
+
+import json
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_09761_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+@pytest.fixture(scope="module")
+def clue_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_09761_gb300 import build, clue
+    build.build()
+    clue.load()
+    return clue
+
+
+def _cl(clue_mod, extent=(-250.0, 250.0, -250.0, 250.0), layers=128, **kw):
+    return clue_mod.Clusterer(device=0, extent=extent, max_layers=layers, **kw)
+
+
+def _gpu_all(cl, ev, params):
+    cid, seed = cl.run(ev.x, ev.y, ev.layer, ev.energy, params)
+    rho, delta, nh = cl.intermediates()
+    cl.sync()
+    return dict(cluster_id=cid.cpu().numpy(), is_seed=seed.cpu().numpy(),
+                rho=rho.cpu().numpy(), delta=delta.cpu().numpy(), nh=nh.cpu().numpy())
+
+
+def _bits(a):
+    return np.ascontiguousarray(a, np.float32).view(np.uint32)
+
+
+def assert_parity(g, ref, keys=("cluster_id", "is_seed", "rho", "delta", "nh")):
+    for k in keys:
+        a, b = g[k], ref[k]
+        if a.dtype.kind == "f":
+            bad = np.nonzero(_bits(a) != _bits(b))[0]
+        else:
+            bad = np.nonzero(a != b.astype(a.dtype))[0]
+        assert bad.size == 0, f"{k}: {bad.size} mismatches, first {bad[:8]}: {a[bad[:8]]} vs {b[bad[:8]]}"
+
+
+class Ev:
+    def __init__(self, x, y, layer, energy):
+        self.x = np.asarray(x, np.float32)
+        self.y = np.asarray(y, np.float32)
+        self.layer = np.asarray(layer, np.int32)
+        self.energy = np.asarray(energy, np.float32)
+        self.n = self.x.shape[0]
+
+
+@pytest.mark.parametrize("name", sorted(p.stem for p in GOLDEN.glob("*.json")))
+def test_golden_fixtures(clue_mod, name):
+    d = json.loads((GOLDEN / f"{name}.json").read_text())
+    cl = _cl(clue_mod, d["extent"], d["n_layers"])
+    g = _gpu_all(cl, Ev(d["x"], d["y"], d["layer"], d["w"]), d["params"])
+    exp = d["expected"]
+    assert g["cluster_id"].tolist() == exp["cluster_id"]
+    assert g["is_seed"].tolist() == exp["is_seed"]
+    assert g["nh"].tolist() == exp["nh"]
+    assert _bits(g["rho"]).tolist() == _bits(np.array(exp["rho"], np.float32)).tolist()
+    d2 = np.array([np.inf if v == "inf" else v for v in exp["delta2"]], np.float32)
+    assert _bits(g["delta"]).tolist() == _bits(np.sqrt(d2)).tolist()
+
+
+CASES = [
+    ("blobs", 2400, 3, gen.PARAMS_BLOBS, 0, (-40.0, 40.0, -40.0, 40.0)),
+    ("blobs", 1500, 1, (2.0, 1.0, 1.0, 3.0), 1, (-40.0, 40.0, -40.0, 40.0)),
+    ("irregular", 20000, 2, gen.PARAMS_IRREGULAR, 2, (-60.0, 60.0, -60.0, 60.0)),
+    ("paper", 20000, 4, gen.PARAMS_PAPER, 3, (-100.0, 100.0, -100.0, 100.0)),
+    ("uniform", 5000, 1, (6.0, 3.0, 4.0, 8.0), 4, (-40.0, 40.0, -40.0, 40.0)),
+    ("blobs", 3000, 2, (2.0, 2.0, 6.0, 1.0), 5, (-40.0, 40.0, -40.0, 40.0)),
+    ("blobs", 10_000, 10, gen.PARAMS_BLOBS, 0, gen.EXTENT),
+    ("irregular", 50_000, 5, gen.PARAMS_IRREGULAR, 7, gen.EXTENT),
+]
+
+
+@pytest.mark.parametrize("kind,n,L,params,seed,ext", CASES)
+def test_parity_vs_oracle(clue_mod, kind, n, L, params, seed, ext):
+    ev = gen.make_event(n, L, seed, kind, extent=ext)
+    cl = _cl(clue_mod, ext, L)
+    g = _gpu_all(cl, ev, params)
+    ref = oracle.run_event(ev, params, L, extent=ext)
+    assert_parity(g, ref)
+
+
+def test_parity_scaling_event_full_size(clue_mod):
+    """100 layers x 10k hits (1M hits), the largest single event of the
+    scaling sweep, compared in full."""
+    ev = gen.scaling_event(10_000, 0)
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    g = _gpu_all(cl, ev, gen.PARAMS_BLOBS)
+    ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 100)
+    assert_parity(g, ref)
+
+
+@pytest.mark.parametrize("bin_size,block", [(2.0, 128), (3.0, 256), (4.5, 512), (9.0, 256),
+                                             (25.0, 128)])
+def test_bin_size_and_block_do_not_change_results(clue_mod, bin_size, block):
+    ext = (-80.0, 80.0, -80.0, 80.0)
+    ev = gen.make_event(30_000, 3, 31, "irregular", extent=ext)
+    ref = oracle.run_event(ev, gen.PARAMS_IRREGULAR, 3, extent=ext)
+    cl = _cl(clue_mod, ext, 3, bin_size=bin_size, block_size=block)
+    assert_parity(_gpu_all(cl, ev, gen.PARAMS_IRREGULAR), ref)
+
+
+def test_batch_equals_events_alone(clue_mod):
+    sizes = [0, 1, 5000, 20000, 0, 1234, 40000, 7]
+    evs = [gen.make_event(n, 100, 500 + i, "blobs") for i, n in enumerate(sizes)]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    cid, seed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    rho, delta, nh = cl.intermediates()
+    cl.sync()
+    cid, seed, rho, nh = (t.cpu().numpy() for t in (cid, seed, rho, nh))
+    for i, ev in enumerate(evs):
+        a, b = offs[i], offs[i + 1]
+        ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 100)
+        assert np.array_equal(cid[a:b], ref["cluster_id"]), i
+        assert np.array_equal(seed[a:b], ref["is_seed"]), i
+        assert np.array_equal(_bits(rho[a:b]), _bits(ref["rho"])), i
+        assert np.array_equal(nh[a:b], ref["nh"]), i
+
+
+def test_repeated_runs_are_identical_and_graph_replay(clue_mod):
+    ev = gen.make_event(60_000, 20, 9, "blobs")
+    cl = _cl(clue_mod, gen.EXTENT, 20, use_graphs=True)
+    outs = []
+    for _ in range(6):  # first direct, second captured, the rest replayed
+        cid, seed = cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_BLOBS)
+        cl.sync()
+        outs.append((cid.cpu().numpy().copy(), seed.cpu().numpy().copy()))
+    ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 20)
+    for c, s in outs:
+        assert np.array_equal(c, ref["cluster_id"]) and np.array_equal(s, ref["is_seed"])
+
+
+def test_host_pointer_path(clue_mod):
+    evs = [gen.make_event(n, 100, 700 + i, "blobs") for i, n in enumerate([3000, 25000, 9000])]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    for _ in range(3):
+        cid, seed = cl.run_batch_host(x, y, l, e, offs, gen.PARAMS_BLOBS)
+        for i, ev in enumerate(evs):
+            ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 100)
+            assert np.array_equal(cid[offs[i]:offs[i + 1]], ref["cluster_id"])
+            assert np.array_equal(seed[offs[i]:offs[i + 1]], ref["is_seed"])
+
+
+def test_edge_cases(clue_mod):
+    cl = _cl(clue_mod, (-10.0, 10.0, -10.0, 10.0), 4)
+    p = (1.0, 0.5, 1.0, 2.0)
+    # empty event: no-op
+    z = np.zeros(0, np.float32)
+    cid, seed = cl.run(z, z, np.zeros(0, np.int32), z, p)
+    cl.sync()
+    assert cid.numel() == 0
+    # one hit
+    g = _gpu_all(cl, Ev([0.3], [0.1], [2], [1.0]), p)
+    assert g["cluster_id"].tolist() == [0] and g["is_seed"].tolist() == [1]
+    # hits far outside the extent fall into edge bins and still cluster right
+    rng = np.random.default_rng(0)
+    ev = Ev(rng.normal(0, 30, 3000), rng.normal(0, 30, 3000), rng.integers(0, 4, 3000),
+            rng.exponential(1.0, 3000))
+    assert_parity(_gpu_all(cl, ev, p), oracle.run_event(ev, p, 4, extent=(-10.0, 10.0, -10.0, 10.0)))
+
+
+def test_dense_cells_use_the_cta_sorter(clue_mod):
+    """Thousands of hits in one bin (beyond the per-slot ranking limit) go
+    through the radix sorter; identical coordinates give exact distance ties."""
+    rng = np.random.default_rng(1)
+    n = 6000
+    x = np.concatenate([rng.normal(0, 0.3, n // 2), np.full(n // 4, 1.5), rng.uniform(-3, 3, n // 4)])
+    y = np.concatenate([rng.normal(0, 0.3, n // 2), np.full(n // 4, -1.0), rng.uniform(-3, 3, n // 4)])
+    w = rng.exponential(1.0, n)
+    ev = Ev(x, y, np.zeros(n, np.int32), w)
+    ext = (-5.0, 5.0, -5.0, 5.0)
+    cl = _cl(clue_mod, ext, 1, bin_size=2.5)
+    p = (0.5, 3.0, 0.7, 1.0)
+    assert_parity(_gpu_all(cl, ev, p), oracle.run_event(ev, p, 1, extent=ext))
+
+
+def test_wide_tree_overflows_queue_and_completes(clue_mod):
+    """2000 hits on a circle of radius 3 around one heavy hit.  They are
+    farther apart than d_c, so each has rho = its own weight 1 (equal, so none
+    is higher than another), and the centre (rho 1000) is every one's
+    nearest-higher within d_m = 4.  The centre's 2000 followers outgrow the
+    expansion queue; the completion pass must still give each the centre's id."""
+    k = 2000
+    ang = np.arange(k) * (2 * np.pi / k)
+    x = np.concatenate([[0.0], 3 * np.cos(ang), [50.0]])
+    y = np.concatenate([[0.0], 3 * np.sin(ang), [50.0]])
+    w = np.concatenate([[1000.0], np.ones(k), [5.0]])
+    ev = Ev(x, y, np.zeros(k + 2, np.int32), w)
+    p = (0.005, 0.5, 4.0, 4.0)
+    ext = (-100.0, 100.0, -100.0, 100.0)
+    cl = _cl(clue_mod, ext, 1)
+    ref = oracle.run_event(ev, p, 1, extent=ext)
+    assert (ref["nh"][1:k + 1] == 0).all() and (ref["cluster_id"][1:k + 1] == 0).all()
+    assert_parity(_gpu_all(cl, ev, p), ref)
+
+
+def test_long_chain(clue_mod):
+    """A line of hits with rising weights: nh chains of length ~1000."""
+    n = 1000
+    x = np.arange(n, dtype=np.float64)
+    w = 1.0 + np.arange(n) * 1e-3
+    ev = Ev(x - 500.0, np.zeros(n), np.zeros(n, np.int32), w)
+    p = (1.5, 1.0, 2.0, 3.0)
+    ext = (-600.0, 600.0, -10.0, 10.0)
+    cl = _cl(clue_mod, ext, 1)
+    ref = oracle.run_event(ev, p, 1, extent=ext)
+    assert_parity(_gpu_all(cl, ev, p), ref)
+
+
+def test_invalid_inputs_reported_at_sync(clue_mod):
+    cl = _cl(clue_mod, gen.EXTENT, 4)
+    x = np.zeros(100, np.float32)
+    x[7] = np.nan
+    cl.run(x, np.zeros(100), np.zeros(100, np.int32), np.ones(100), gen.PARAMS_BLOBS)
+    with pytest.raises(clue_mod.ClueError) as ei:
+        cl.sync()
+    assert ei.value.code == clue_mod.CLUE_ERR_INPUT
+    cl.sync()  # error cleared
+    bad_layer = np.full(50, 4, np.int32)
+    cl.run(np.zeros(50), np.zeros(50), bad_layer, np.ones(50), gen.PARAMS_BLOBS)
+    with pytest.raises(clue_mod.ClueError):
+        cl.sync()
+    with pytest.raises(clue_mod.ClueError) as ei:
+        cl.run(np.zeros(5), np.zeros(5), np.zeros(5, np.int32), np.ones(5), (0.0, 1.0, 1.0, 1.0))
+    assert ei.value.code == clue_mod.CLUE_ERR_ARG
+
+
+def test_autotune_keeps_results(clue_mod):
+    evs = [gen.make_event(n, 100, 900 + i, "blobs") for i, n in enumerate([15000, 60000, 200000])]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    table = cl.autotune(x, y, l, e, offs, gen.PARAMS_BLOBS, reps=1)
+    assert "block" in table
+    cid, seed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    cl.sync()
+    cid = cid.cpu().numpy()
+    for i, ev in enumerate(evs):
+        assert np.array_equal(cid[offs[i]:offs[i + 1]],
+                              oracle.run_event(ev, gen.PARAMS_BLOBS, 100)["cluster_id"])
+    cl.tuning = table  # round-trips through the text format
+
+
+def test_stage_times_and_launch_count(clue_mod):
+    ev = gen.make_event(100_000, 100, 3, "blobs")
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    cl.set_profiling(True)
+    cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_BLOBS)
+    st = cl.stage_times()
+    assert list(st) == ["grid_fill", "rho", "nh_delta", "decide_followers", "expand"]
+    assert all(v >= 0 for v in st.values())
+    assert cl.launch_count() == 16
