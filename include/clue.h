@@ -180,6 +180,45 @@ int32_t clue_last_launch_count(clue_ctx *ctx);
 /* Device bytes the context's scratch arena holds now. */
 int64_t clue_scratch_bytes(clue_ctx *ctx);
 
+/*
+ * Single-event clustering that allocates nothing (the paper has no
+ * counterpart: this is a deployment variant of clue_run).
+ *
+ * For callers that cannot allocate device memory -- code running inside
+ * another framework's memory pool, a real-time loop where an allocation could
+ * block or fail, or a plugin whose host owns every device allocation.  It runs
+ * the same kernels as clue_run, so results are bit-identical to clue_run's,
+ * but every scratch array lives in one fixed array in the library's device
+ * memory (about 12.9 MB, held on every GPU that loads the library until the
+ * process exits).  It needs no context and calls no allocator, neither CUDA's
+ * nor any other.
+ *
+ *   x, y, layer, energy, cluster_id, is_seed: DEVICE arrays of n entries on
+ *     the current device, as in clue_run (caller-owned)
+ *   n          0 <= n <= CLUE_STATIC_MAX_HITS (larger n: CLUE_ERR_ARG, nothing runs)
+ *   dc, rhoc, delta_c, delta_o: as in clue_run
+ *   x_min..y_max, max_layers: the grid extent and layer count (as clue_opts);
+ *     max_layers * (bins per layer) must fit CLUE_STATIC_MAX_CELLS, else the
+ *     bins are widened (results do not depend on the bin size)
+ *   stream     cudaStream_t to run on (NULL = the legacy default stream)
+ *
+ * The call is synchronous: it returns after the results are in cluster_id /
+ * is_seed, with CLUE_OK, CLUE_ERR_ARG, CLUE_ERR_INPUT (NaN/Inf or bad layer,
+ * outputs unspecified), CLUE_ERR_TIMEOUT or CLUE_ERR_CUDA.
+ * The first call on each device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and keeps what the previous call
+ * left in it (the call clears what must start at zero): calls that overlap on
+ * the GPU -- from several host threads or on several streams at once -- race
+ * and give wrong results.
+ */
+#define CLUE_STATIC_MAX_HITS 65536
+#define CLUE_STATIC_MAX_CELLS 1048576
+int clue_run_static(const float *x, const float *y, const int32_t *layer, const float *energy,
+                    int64_t n, float dc, float rhoc, float delta_c, float delta_o, float x_min,
+                    float x_max, float y_min, float y_max, int32_t max_layers,
+                    int32_t *cluster_id, uint8_t *is_seed, void *stream);
+
 /* Human-readable text of a CLUE_ERR_* code. */
 const char *clue_strerror(int code);
 

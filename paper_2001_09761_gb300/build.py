@@ -19,7 +19,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libclue.so"
-SOURCES = ["clue_api.cu", "k_grid.cu", "k_density.cu", "k_assign.cu"]
+SOURCES = ["clue_api.cu", "k_grid.cu", "k_density.cu", "k_assign.cu", "clue_static.cu"]
 HEADERS = ["clue_internal.h", "device_common.cuh", "scan.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -28,7 +28,7 @@ ABI_SYMBOLS = [
     "clue_run_batch", "clue_run_batch_host", "clue_sync", "clue_get_intermediates",
     "clue_autotune", "clue_get_tuning", "clue_set_tuning", "clue_set_profiling",
     "clue_stage_times", "clue_last_launch_count", "clue_scratch_bytes", "clue_strerror",
-    "clue_last_message", "clue_version",
+    "clue_last_message", "clue_version", "clue_run_static",
 ]
 
 
@@ -84,6 +84,8 @@ def load(path: os.PathLike | None = None):
         "clue_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "clue_last_message": (ctypes.c_char_p, [P]),
         "clue_version": (ctypes.c_char_p, []),
+        "clue_run_static": (ctypes.c_int, [P, P, P, P, I64, F, F, F, F, F, F, F, F, I32, P, P,
+                                           P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -205,6 +207,18 @@ def clue_last_message(ctx) -> str:
 
 def clue_version() -> str:
     return load().clue_version().decode()
+
+
+#: Largest event clue_run_static accepts (CLUE_STATIC_MAX_HITS).
+CLUE_STATIC_MAX_HITS = 65536
+
+
+def clue_run_static(x, y, layer, energy, n, dc, rhoc, delta_c, delta_o, x_min, x_max, y_min,
+                    y_max, max_layers, cluster_id, is_seed, stream) -> int:
+    """Single event with all scratch in the library's fixed device array
+    (no allocation); synchronous on ``stream``."""
+    return load().clue_run_static(x, y, layer, energy, n, dc, rhoc, delta_c, delta_o, x_min,
+                                  x_max, y_min, y_max, max_layers, cluster_id, is_seed, stream)
 
 
 # ---- torch-facing wrapper ---------------------------------------------------

@@ -1,0 +1,237 @@
+// clue_run_static: single-event clustering with no device allocation at all.
+//
+// Some callers cannot call cudaMalloc: code that runs inside a framework's
+// memory pool or a real-time loop where any allocation may block or fail,
+// plugins whose host owns every device allocation, or code that must keep its
+// footprint fixed at load time.  For them this entry point runs the same
+// pipeline as clue_run (the same kernels, so the same results bit for bit)
+// with every scratch array placed in one file-scope __device__ array of fixed
+// size, STATIC_BYTES below, which every GPU that loads the library holds until
+// the process exits.  No context is needed; the caller passes inputs, outputs
+// and a stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "clue.h"
+#include "clue_internal.h"
+#include "scan.cuh"
+
+using namespace clue;
+
+namespace {
+
+constexpr int64_t STATIC_MAX_HITS = CLUE_STATIC_MAX_HITS;
+constexpr int64_t STATIC_MAX_CELLS = CLUE_STATIC_MAX_CELLS;
+constexpr int64_t STATIC_MAX_TILES = (STATIC_MAX_HITS + TILE - 1) / TILE;
+constexpr int64_t STATIC_PARTS =
+    (std::max(STATIC_MAX_HITS, STATIC_MAX_CELLS) + SCAN_TILE - 1) / SCAN_TILE + 2;
+
+constexpr size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+constexpr size_t NB = (size_t)STATIC_MAX_HITS, CB = (size_t)STATIC_MAX_CELLS;
+
+// Byte layout of the scratch array (offsets in order of the Buffers fields).
+constexpr size_t STATIC_BYTES =
+    al(sizeof(Ctrl)) + al(sizeof(EventDesc)) + al(STATIC_MAX_TILES * sizeof(Tile)) +
+    al(NB * 4) /*key*/ + al(CB * 4) /*count*/ + al((CB + 1) * 4) /*cell_start*/ +
+    al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ + al((NB / SMALL_SEGMENT + 1) * 4) /*big*/ +
+    al(NB * 4) /*ids_s*/ + 3 * al(NB * 4) /*xs ys ws*/ + al(NB * 4) /*lay_s*/ +
+    al(NB * 4) /*rho_s*/ + al(NB * 4) /*rho*/ + al(NB * 4) /*delta2*/ + al(NB * 4) /*nh*/ +
+    al(NB) /*flags*/ + al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
+    al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/;
+
+}  // namespace
+
+// The scratch itself.  Host code must not pass this name to a kernel: on the
+// host it is only a stand-in symbol; the device address comes from
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_BYTES];
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_setup_mutex;
+void *g_scratch_ptr[MAX_DEVICES] = {};
+
+// Once per device, with that device current: the device address of the array.
+int scratch_address(int dev, void **out) {
+    if (dev < 0 || dev >= MAX_DEVICES) return CLUE_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return CLUE_ERR_CUDA;
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return CLUE_OK;
+}
+
+bool finite_nonneg(float d) { return std::isfinite(d) && d >= 0.0f && d <= 1e18f; }
+
+}  // namespace
+
+extern "C" int clue_run_static(const float *x, const float *y, const int32_t *layer,
+                               const float *energy, int64_t n, float dc, float rhoc,
+                               float delta_c, float delta_o, float x_min, float x_max,
+                               float y_min, float y_max, int32_t max_layers,
+                               int32_t *cluster_id, uint8_t *is_seed, void *stream) {
+    if (n < 0 || n > STATIC_MAX_HITS) return CLUE_ERR_ARG;
+    if (!(dc >= 1e-18f) || !finite_nonneg(dc) || !finite_nonneg(delta_c) ||
+        !finite_nonneg(delta_o) || !std::isfinite(rhoc))
+        return CLUE_ERR_ARG;
+    if (!std::isfinite(x_min) || !std::isfinite(x_max) || !std::isfinite(y_min) ||
+        !std::isfinite(y_max) || !(x_max > x_min) || !(y_max > y_min) || max_layers < 1 ||
+        (int64_t)max_layers > STATIC_MAX_CELLS)
+        return CLUE_ERR_ARG;
+    if (n == 0) return CLUE_OK;
+    if (!x || !y || !layer || !energy || !cluster_id || !is_seed) return CLUE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CLUE_ERR_CUDA;
+    void *base = nullptr;
+    int rc = scratch_address(dev, &base);
+    if (rc) return rc;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CLUE_ERR_CUDA;
+
+    // Grid: the bin size only changes speed, never results; widen the bins
+    // until the grid fits the static cell budget.
+    const double wx = (double)x_max - x_min, wy = (double)y_max - y_min;
+    double sbin = std::max((double)dc, 6.0 * dc * 1.001);
+    int64_t nbx = 1, nby = 1;
+    const double cap = std::min<double>(16.0 * (double)n + 64.0 * max_layers,
+                                        (double)STATIC_MAX_CELLS);
+    for (int it = 0; it < 200; ++it) {
+        nbx = std::max<int64_t>(1, (int64_t)std::ceil(wx / sbin));
+        nby = std::max<int64_t>(1, (int64_t)std::ceil(wy / sbin));
+        if ((double)nbx * nby * max_layers <= cap) break;
+        sbin *= 1.1;
+    }
+    const int64_t C = (int64_t)max_layers * nbx * nby;
+    if (C > STATIC_MAX_CELLS) return CLUE_ERR_ARG;
+
+    // Carve the arrays in the order of STATIC_BYTES.
+    char *p = (char *)base;
+    auto take = [&](size_t bytes) {
+        void *r = p;
+        p += al(bytes);
+        return r;
+    };
+    Buffers b{};
+    Ctrl *ctrl = (Ctrl *)take(sizeof(Ctrl));
+    EventDesc *d_ev = (EventDesc *)take(sizeof(EventDesc));
+    Tile *d_tiles = (Tile *)take(STATIC_MAX_TILES * sizeof(Tile));
+    b.key = (int32_t *)take(NB * 4);
+    b.count = (int32_t *)take(CB * 4);
+    b.cell_start = (int32_t *)take((CB + 1) * 4);
+    b.perm = (int32_t *)take(NB * 4);
+    b.tmp = (int32_t *)take(NB * 4);
+    b.big = (int32_t *)take((NB / SMALL_SEGMENT + 1) * 4);
+    b.ids_s = (int32_t *)take(NB * 4);
+    b.xs = (float *)take(NB * 4);
+    b.ys = (float *)take(NB * 4);
+    b.ws = (float *)take(NB * 4);
+    b.lay_s = (int32_t *)take(NB * 4);
+    b.rho_s = (float *)take(NB * 4);
+    b.rho = (float *)take(NB * 4);
+    b.delta2 = (float *)take(NB * 4);
+    b.nh = (int32_t *)take(NB * 4);
+    b.flags = (uint8_t *)take(NB);
+    b.fcount = (int32_t *)take(NB * 4);
+    b.hs = (unsigned long long *)take((NB + 1) * 8);
+    b.fol = (int32_t *)take(NB * 4);
+    b.seed_list = (int32_t *)take(NB * 4);
+    b.scan_partials = take((size_t)STATIC_PARTS * 8);
+    b.scan_partials_cap = STATIC_PARTS;
+    if ((size_t)(p - (char *)base) > STATIC_BYTES) return CLUE_ERR_STATE;
+
+    // The plan of one event: its descriptor and its tiles.
+    struct {
+        EventDesc ev;
+        Tile tiles[STATIC_MAX_TILES];
+    } host;
+    std::memset(&host, 0, sizeof(host));
+    host.ev.hit_off = 0;
+    host.ev.cell_off = 0;
+    host.ev.n = (int32_t)n;
+    host.ev.nbx = (int32_t)nbx;
+    host.ev.nby = (int32_t)nby;
+    host.ev.xmin = x_min;
+    host.ev.ymin = y_min;
+    host.ev.inv_s = (float)(1.0 / sbin);
+    int ntiles = 0;
+    for (int64_t t = 0; t < n; t += TILE)
+        host.tiles[ntiles++] = Tile{(int32_t)t, (int32_t)std::min<int64_t>(TILE, n - t), 0, 0};
+
+    b.x = x;
+    b.y = y;
+    b.w = energy;
+    b.layer = layer;
+    b.cid = cluster_id;
+    b.is_seed = is_seed;
+    b.events = d_ev;
+    b.tiles = d_tiles;
+    b.ntiles = ntiles;
+    b.nevents = 1;
+    b.N = n;
+    b.C = C;
+    b.ctrl = ctrl;
+
+    Params prm;
+    const float dm = delta_o > delta_c ? delta_o : delta_c;
+    prm.dc2 = dc * dc;
+    prm.dm2 = dm * dm;
+    prm.dcs2 = delta_c * delta_c;
+    prm.dos2 = delta_o * delta_o;
+    prm.rhoc = rhoc;
+    prm.rwin_rho = dc * (1.0f + 0x1p-12f);
+    prm.rwin_nh = dm * (1.0f + 0x1p-12f);
+    prm.L = max_layers;
+    LaunchCfg cfg;
+    cfg.block_fill = 256;
+    cfg.block_density = 256;
+    cfg.grid_cap = sms * 8;
+
+#define SCK(call)                                            \
+    do {                                                     \
+        if ((call) != cudaSuccess) {                         \
+            cudaGetLastError();                              \
+            return CLUE_ERR_CUDA;                            \
+        }                                                    \
+    } while (0)
+    // The array keeps the previous call's contents: reset what must start at
+    // zero (control word, per-cell counters); every other array is fully
+    // written before it is read.
+    SCK(cudaMemcpyAsync(d_ev, &host.ev, sizeof(EventDesc), cudaMemcpyHostToDevice, s));
+    SCK(cudaMemcpyAsync(d_tiles, host.tiles, ntiles * sizeof(Tile), cudaMemcpyHostToDevice, s));
+    SCK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    SCK(cudaMemsetAsync(b.count, 0, (size_t)C * 4, s));
+    int nl = 0;
+    SCK(launch_fill_count(b, prm, cfg, s));
+    SCK(launch_scan_cells(b, cfg, s, &nl));
+    SCK(launch_fill_scatter(b, cfg, s));
+    SCK(launch_fill_canon(b, cfg, s));
+    SCK(launch_fill_big(b, cfg, s));
+    SCK(launch_rho(b, prm, cfg, s));
+    SCK(launch_nh(b, prm, cfg, s));
+    SCK(launch_decide(b, prm, cfg, s));
+    SCK(launch_scan_hits(b, cfg, s, &nl));
+    SCK(launch_link(b, cfg, s));
+    SCK(launch_expand(b, cfg, s));
+    SCK(launch_complete(b, cfg, s));
+    Ctrl h{};
+    SCK(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    SCK(cudaStreamSynchronize(s));
+#undef SCK
+    if (h.err & ERRBIT_INPUT) return CLUE_ERR_INPUT;
+    if (h.err) return CLUE_ERR_TIMEOUT;
+    return CLUE_OK;
+}
