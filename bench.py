@@ -32,11 +32,6 @@ PARAMS = gen.PARAMS_BLOBS
 METRIC = "CLUE Mhits/s on 1 GB300, batched vs per-event; p50/p99 event latency"
 WORKLOAD = ("256 uneven events in one batch: hits log-uniform 10k-1M, 100 layers, "
             "blob/noise generator, d_c=2 rho_c=2 delta_c=2 delta_o=4")
-# algorithmic bytes per hit of the density kernels (own hit read once, outputs
-# written once): rho reads x, y, w, layer and writes rho; nh/delta reads x, y,
-# rho, layer and writes rho, delta^2, nh.
-ALG_BYTES = {"rho": 20, "nh_delta": 28, "grid_fill": 16 + 4 + 4 + 16 + 4,
-             "decide_followers": 12 + 5 + 8 + 4, "expand": 8}
 
 
 def dist_env():
@@ -109,9 +104,8 @@ def load_peaks():
 
 
 def make_workload(rank: int, n_events: int, lo: float, hi: float):
-    # weak scaling: each rank clusters its own batch of the same size
-    events = gen.uneven_batch(n_events, lo, hi, size_seed=rank, first_event_seed=1000 + 100000 * rank)
-    return events
+    from paper_2001_09761_gb300 import replicas
+    return gen.uneven_batch(n_events, lo, hi, *replicas.weak_seeds(rank))
 
 
 def cpu_oracle_sample(events, budget_s: float):
@@ -166,11 +160,131 @@ def run_reference(args):
     }))
 
 
+# Algorithmic bytes per hit of each kernel: every array the step needs is
+# read once and every result written once (no re-reads, no scratch beyond
+# the stage's own outputs).
+ALG_BYTES = {
+    "fill_count": 16 + 4 + 4 + 4,      # x, y, w, layer in; key, follower counter, cell count
+    "fill_scatter": 4 + 4 + 4,         # key, cell offset in; slot out
+    "fill_canon": 4 + 4 + 8 + 12 + 20,  # slot, key, cell range, x/y/w in; sorted copies out
+    "rho": 16 + 4,                     # x, y, w, layer in; rho out
+    "nh_delta": 16 + 12,               # x, y, rho, layer in; rho, delta^2, nh out
+    "decide": 12 + 1 + 4,              # rho, delta^2, nh in; flags, follower count out
+    "link": 1 + 8 + 4 + 4 + 1 + 4,     # flags, prefix, nh in; id, seed flag, list slot out
+    "expand_level": 8 + 4 + 4 + 4,     # list range, parent id, follower in; id out
+    "complete": 4 + 4,                 # id in, id out
+}
+
+
+def parse_traffic():
+    """Per-kernel DRAM bytes per hit from the committed ncu summary, keyed by
+    kernel, with the source hash they were taken at (None if absent)."""
+    p = ROOT / "profiles" / "traffic.md"
+    out = {}
+    if not p.exists():
+        return out
+    for line in p.read_text().splitlines():
+        f = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(f) >= 4 and f[0] in ALG_BYTES:
+            try:
+                out[f[0]] = (float(f[1]), f[3])
+            except ValueError:
+                pass
+    return out
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2001_09761_gb300" / "csrc").glob("*")):
+        h.update(f.read_bytes())
+    return h.hexdigest()[:12]
+
+
+def timed_runs(cl, fn, reps):
+    """Latency of `reps` synchronous calls (ms list)."""
+    lat = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        cl.sync()
+        lat.append((time.perf_counter() - t0) * 1e3)
+    return lat
+
+
+def extra_configs(torch, clue, tuning, dev, args):
+    """The other workloads: each reported as Mhits/s (and latency)."""
+    res = {}
+    def single(ev, layers, params, reps, key):
+        cl = clue.Clusterer(device=dev.index, extent=gen.EXTENT, max_layers=layers)
+        cl.tuning = tuning
+        x, y = torch.from_numpy(ev.x).to(dev), torch.from_numpy(ev.y).to(dev)
+        l, e = torch.from_numpy(ev.layer).to(dev), torch.from_numpy(ev.energy).to(dev)
+        cid = torch.empty(ev.n, dtype=torch.int32, device=dev)
+        seed = torch.empty(ev.n, dtype=torch.uint8, device=dev)
+        run = lambda: cl.run(x, y, l, e, params, out=(cid, seed))
+        for _ in range(3):
+            run()
+        cl.sync()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(cl.stream)
+        for _ in range(reps):
+            run()
+        s1.record(cl.stream)
+        s1.synchronize()
+        ms = s0.elapsed_time(s1) / reps
+        lat = np.array(timed_runs(cl, run, reps))
+        cl.close()
+        return {"mhits_per_s": ev.n / (ms * 1e-3) / 1e6, "device_ms": ms,
+                "latency_p50_ms": float(np.percentile(lat, 50)),
+                "latency_p99_ms": float(np.percentile(lat, 99)), "hits": ev.n}
+
+    res["single_10k"] = single(gen.single_event_10k(0), 10, PARAMS, 200, "c1")
+    sweep = {}
+    for h in range(1000, 10001, 1000 if args.full else 3000):
+        vals = [single(gen.scaling_event(h, s), 100, PARAMS, 10, "c2")["mhits_per_s"]
+                for s in range(args.sweep_seeds)]
+        sweep[str(100 * h)] = float(np.median(vals))
+    res["scaling_sweep_median_mhits_per_s"] = sweep
+    irr = gen.irregular_event(0)
+    res["irregular_5M"] = single(irr, 50, gen.PARAMS_IRREGULAR, 5, "c4")
+    return res
+
+
+def served(torch, clue, tuning, dev, peak_mhits, args):
+    from paper_2001_09761_gb300 import serve
+    rng_sizes = gen.batch_sizes(args.pool, 1e4, 2e6, seed=7)
+    pool = []
+    for k, n in enumerate(rng_sizes):
+        ev = gen.make_event(int(n), 100, 5000 + k, "blobs")
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        pool.append((pin(ev.x), pin(ev.y), pin(ev.layer), pin(ev.energy)))
+    mean_hits = float(np.mean(rng_sizes))
+    out = {"pool_events": len(pool), "mean_hits": mean_hits, "loads": {}}
+    for load in args.loads:
+        be = serve.GpuBackend(device=dev.index, extent=gen.EXTENT, max_layers=100,
+                              params=PARAMS, region_hits=16_000_000, n_regions=3, tuning=tuning)
+        free, _ = torch.cuda.mem_get_info(dev)
+        srv = serve.Server(be, mem_budget_bytes=int(0.5 * free))
+        rate = load * peak_mhits * 1e6 / mean_hits
+        serve.offered_load(srv, pool[:2], rate_events_per_s=1e3, n_requests=4, seed=1)  # warm
+        srv2 = srv
+        srv2.lat, srv2.done_hits, srv2.t_first, srv2.t_last = [], 0, None, None
+        srv2.batches, srv2.batch_sizes = 0, []
+        serve.offered_load(srv2, pool, rate_events_per_s=rate, n_requests=args.requests,
+                           seed=int(load * 100))
+        st = srv2.stats()
+        srv2.close()
+        st["offered_events_per_s"] = rate
+        out["loads"][str(load)] = st
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--events", type=int, default=256)
     ap.add_argument("--lo", type=float, default=1e4)
@@ -178,57 +292,68 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--per-event-sample", type=int, default=64)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
+    ap.add_argument("--full", action="store_true", help="full sweep and request counts")
+    ap.add_argument("--sweep-seeds", type=int, default=2)
+    ap.add_argument("--pool", type=int, default=32)
+    ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--loads", type=float, nargs="*", default=[0.1, 0.5, 0.9])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.full:
+        args.sweep_seeds, args.requests = 10, 2000
+        args.loads = [0.1, 0.25, 0.5, 0.75, 0.9, 1.0]
     if args.impl == "reference":
         return run_reference(args)
 
     import torch
+    from paper_2001_09761_gb300 import clue, replicas
     ws, rank, local = dist_env()
-    pg = None
+    dist = None
     if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-        pg = dist
+        import torch.distributed as tdist
+        tdist.init_process_group("gloo")
+        dist = tdist
     torch.cuda.set_device(local)
-    from paper_2001_09761_gb300 import clue
+    dev = torch.device("cuda", local)
 
-    events = make_workload(rank, args.events, args.lo, args.hi)
+    size_seed, ev_seed = replicas.weak_seeds(rank)
+    events = gen.uneven_batch(args.events, args.lo, args.hi, size_seed, ev_seed)
     x, y, l, e, offs = gen.concat(events)
     N = int(offs[-1])
-    dev = torch.device("cuda", local)
     tx, ty = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
     tl, te = torch.from_numpy(l).to(dev), torch.from_numpy(e).to(dev)
     cid = torch.empty(N, dtype=torch.int32, device=dev)
     seed = torch.empty(N, dtype=torch.uint8, device=dev)
     cl = clue.Clusterer(device=local, extent=gen.EXTENT, max_layers=100)
     if not args.no_autotune:
-        cl.autotune(tx, ty, tl, te, offs, PARAMS, reps=1)
+        cl.autotune(tx, ty, tl, te, offs, PARAMS, reps=3)
+    tuning = cl.tuning
     cl.set_profiling(True)
     for _ in range(args.warmup):
         cl.run_batch(tx, ty, tl, te, offs, PARAMS, out=(cid, seed))
     cl.sync()
     try:
-        cl.stage_times()
-    except clue.ClueError as exc:  # stage events not timeable in a replayed graph
-        print(f"stage timing in graph mode failed ({exc}: {clue.clue_last_message(cl.ctx)}); "
+        cl.kernel_times()
+    except clue.ClueError as exc:  # events not timeable in a replayed graph
+        print(f"kernel timing in graph mode failed ({exc}: {clue.clue_last_message(cl.ctx)}); "
               "timing with direct launches", file=sys.stderr)
-        table = cl.tuning
         cl = clue.Clusterer(device=local, extent=gen.EXTENT, max_layers=100, use_graphs=False)
-        cl.tuning = table
+        cl.tuning = tuning
         cl.set_profiling(True)
         for _ in range(args.warmup):
             cl.run_batch(tx, ty, tl, te, offs, PARAMS, out=(cid, seed))
         cl.sync()
     torch.cuda.synchronize()
 
-    # ---- timed region: batched steps -------------------------------------
+    # ---- timed region: batched steps (graph replay) -----------------------
     clocks = ClockSampler(local)
     clocks.start()
-    stage_sum = {}
-    if pg:
-        pg.barrier()
+    time.sleep(0.3)
+    kern = {}
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
@@ -237,32 +362,32 @@ def main():
     for _ in range(args.steps):
         cl.run_batch(tx, ty, tl, te, offs, PARAMS, out=(cid, seed))
         launches += cl.launch_count()
-        for k, v in cl.stage_times().items():  # waits for this step's stage events
-            stage_sum[k] = stage_sum.get(k, 0.0) + v
+        for k, v in cl.kernel_times().items():  # waits for this step's events
+            kern[k] = kern.get(k, 0.0) + v
     stop.record(cl.stream)
     stop.synchronize()
     torch.cuda.synchronize()
-    ms = start.elapsed_time(stop)
-    if pg:
-        t = torch.tensor([ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    if dist:
+        dist.barrier()
     clk = clocks.stop()
+    ms, hits_all = replicas.reduce_timing(start.elapsed_time(stop), N, dist)
     cl.sync()
     ms_per_step = ms / args.steps
-    value = N * ws / (ms_per_step * 1e-3) / 1e6
-    stages = {k: v / args.steps for k, v in stage_sum.items()}
+    value = hits_all / (ms_per_step * 1e-3) / 1e6
+    kern = {k: v / args.steps for k, v in kern.items()}
+    stages = {}
+    for k, v in kern.items():
+        stages[clue.STAGE_OF.get(k, k)] = stages.get(clue.STAGE_OF.get(k, k), 0.0) + v
 
     # ---- per-event launches (same events, one clue_run each) -------------
     cl_pe = clue.Clusterer(device=local, extent=gen.EXTENT, max_layers=100, use_graphs=False)
-    cl_pe.tuning = cl.tuning
+    cl_pe.tuning = tuning
     idx = np.linspace(0, len(events) - 1, min(args.per_event_sample, len(events))).astype(int)
     pe_hits = int(sum(events[i].n for i in idx))
     views = [(int(offs[i]), int(offs[i + 1])) for i in idx]
     for a, b in views[:3]:
         cl_pe.run(tx[a:b], ty[a:b], tl[a:b], te[a:b], PARAMS, out=(cid[a:b], seed[a:b]))
     cl_pe.sync()
-    lat = []
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     s0.record(cl_pe.stream)
@@ -271,12 +396,14 @@ def main():
     s1.record(cl_pe.stream)
     s1.synchronize()
     per_event_value = pe_hits / (s0.elapsed_time(s1) * 1e-3) / 1e6
-    for a, b in views:  # latency of one event alone, device-resident input
+    lat = []
+    for a, b in views:  # one event alone, device-resident input, launch to sync
         t0 = time.perf_counter()
         cl_pe.run(tx[a:b], ty[a:b], tl[a:b], te[a:b], PARAMS, out=(cid[a:b], seed[a:b]))
         cl_pe.sync()
         lat.append((time.perf_counter() - t0) * 1e3)
     lat = np.array(lat)
+    cl_pe.close()
 
     # ---- end to end through the host-pointer entry point -------------------
     hx = torch.from_numpy(x).pin_memory().numpy()
@@ -286,26 +413,38 @@ def main():
     hcid = torch.empty(N, dtype=torch.int32).pin_memory().numpy()
     hseed = torch.empty(N, dtype=torch.uint8).pin_memory().numpy()
     cl_h = clue.Clusterer(device=local, extent=gen.EXTENT, max_layers=100)
-    cl_h.tuning = cl.tuning
+    cl_h.tuning = tuning
     for _ in range(2):
         cl_h.run_batch_host(hx, hy, hl, he, offs, PARAMS, out=(hcid, hseed))
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, args.steps // 4)
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         cl_h.run_batch_host(hx, hy, hl, he, offs, PARAMS, out=(hcid, hseed))
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value = N * ws / e2e_s / 1e6
+    e2e_ms, _ = replicas.reduce_timing((time.perf_counter() - t0) * 1e3 / e2e_steps, N, dist)
+    e2e_value = hits_all / (e2e_ms * 1e-3) / 1e6
     ok = bool(np.array_equal(hcid, cid.cpu().numpy()))
+    cl_h.close()
 
     # ---- roofline of the dominant kernel ------------------------------------
-    dom = max(stages, key=stages.get)
+    dom = max((k for k in kern if k in ALG_BYTES), key=kern.get)
     peak, peak_kind = load_peaks()
-    achieved = ALG_BYTES[dom] * N / (stages[dom] * 1e-3) / 1e9
+    achieved = ALG_BYTES[dom] * N / (kern[dom] * 1e-3) / 1e9
+    traffic = None
+    tr = parse_traffic()
+    if dom in tr and tr[dom][1] == source_hash():
+        traffic = tr[dom][0] * N
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_hit": ALG_BYTES[dom],
-                "stage_ms": stages}
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
+                "alg_bytes_per_hit": ALG_BYTES[dom], "kernel_ms_per_step": kern,
+                "stage_ms_per_step": stages}
 
+    extra, srv = None, None
+    if rank == 0 and not args.no_extra:
+        extra = extra_configs(torch, clue, tuning, dev, args)
+        srv = served(torch, clue, tuning, dev, value / ws, args)
     cpu = None
     if rank == 0:
         v, desc = cpu_oracle_sample(events, args.cpu_budget)
@@ -318,10 +457,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": len(events) * ws,
-                       "hits_per_step": N * ws, "parallelism": f"replicas x{ws}",
-                       "l2": "inputs (1 GB) larger than L2, no flush"},
+                       "hits_per_step": hits_all, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs (1 GB per rank) larger than L2, no flush"},
             "per_event": {"value": per_event_value, "unit": "Mhits/s", "events": len(idx),
-                          "hits": pe_hits},
+                          "hits": pe_hits, "kind": "one clue_run per event, back to back"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99)),
                            "kind": "one event alone, device-resident input, launch to sync"},
@@ -331,10 +470,12 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,
-            "tuning": cl.tuning,
+            "configs": extra,
+            "served": srv,
+            "tuning": tuning,
         }))
-    if pg:
-        pg.destroy_process_group()
+    if dist:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -65,7 +65,8 @@ typedef struct clue_opts {
     float y_min, y_max;
     int32_t max_layers;  /* layer ids must lie in [0, max_layers) */
     float bin_size;      /* grid bin size (cm); 0 = from the tuning table */
-    int32_t block_size;  /* threads per block of the density kernels; 0 = tuned */
+    int32_t block_size;  /* threads per block of the density kernels (32..256, a
+                            multiple of 32); 0 = tuned */
     int32_t use_graphs;  /* 1 = capture a repeated call into a CUDA graph and replay it */
     void *stream;        /* cudaStream_t to queue work on; NULL = context-owned stream */
 } clue_opts;
@@ -146,11 +147,13 @@ int clue_sync(clue_ctx *ctx);
 int clue_get_intermediates(clue_ctx *ctx, float *rho, float *delta, int32_t *nh);
 
 /*
- * Tune the grid bin size and the density kernels' block size per event-size
- * class on the given device batch (same arguments as clue_run_batch; results
- * of the trial runs are written to cluster_id / is_seed).  Every candidate
- * gives bit-identical results; only speed differs.  `reps` timed repetitions
- * per candidate (>= 1).  Synchronises.  Errors as clue_run_batch.
+ * Tune the grid bin size per event-size class (each class timed on its own
+ * events, copied into a context-owned sub-batch) and the density kernels'
+ * block size (timed on the whole batch) for the given device batch (same
+ * arguments as clue_run_batch; results of the trial runs are written to
+ * cluster_id / is_seed).  Every candidate gives bit-identical results; only
+ * speed differs.  `reps` timed repetitions per candidate (>= 1).
+ * Synchronises.  Errors as clue_run_batch.
  */
 int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
                   const float *energy, const int64_t *offsets, int32_t n_events, float dc,
@@ -166,11 +169,13 @@ int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap);
  * Errors: CLUE_ERR_ARG on malformed text. */
 int clue_set_tuning(clue_ctx *ctx, const char *text);
 
-/* Per-stage timing: when on (1), the next runs record a CUDA event between
- * pipeline stages.  clue_stage_times waits for the last run and writes up to
- * `cap` stage durations in ms (order: grid fill, rho, nh/delta, decide and
- * follower lists, expand) and their names (comma-separated, into names if not
- * NULL, capacity names_cap); returns the number of stages or a negative code. */
+/* Per-kernel timing: when on (1), the next runs record a CUDA event before
+ * the first kernel and after each kernel (or launch group: a prefix sum's
+ * three kernels count as one).  clue_stage_times waits for the last run and
+ * writes up to `cap` durations in ms, in launch order, and their names
+ * (comma-separated, into names if not NULL, capacity names_cap); it returns
+ * the number of entries, or a negative CLUE_ERR_* code (-CLUE_ERR_STATE when
+ * no profiled run exists). */
 int clue_set_profiling(clue_ctx *ctx, int32_t on);
 int clue_stage_times(clue_ctx *ctx, float *ms, int32_t cap, char *names, int64_t names_cap);
 

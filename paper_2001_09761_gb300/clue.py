@@ -181,12 +181,21 @@ def clue_set_profiling(ctx, on: bool) -> int:
 
 
 def clue_stage_times(ctx):
-    ms = (ctypes.c_float * 16)()
-    names = ctypes.create_string_buffer(256)
-    n = load().clue_stage_times(ctx, ms, 16, names, 256)
+    """[(kernel name, ms), ...] of the last profiled run, in launch order."""
+    ms = (ctypes.c_float * 64)()
+    names = ctypes.create_string_buffer(2048)
+    n = load().clue_stage_times(ctx, ms, 64, names, 2048)
     if n < 0:
         raise ClueError(-n, "clue_stage_times")
-    return dict(zip(names.value.decode().split(","), list(ms)[:n]))
+    return list(zip(names.value.decode().split(","), list(ms)[:n]))
+
+
+#: Pipeline step of each profiled kernel (S1 grid fill .. S5 expansion).
+STAGE_OF = {"fill_count": "grid_fill", "scan_cells": "grid_fill", "fill_scatter": "grid_fill",
+            "fill_canon": "grid_fill", "fill_big": "grid_fill", "rho": "rho",
+            "nh_delta": "nh_delta", "decide": "decide_followers",
+            "scan_hits": "decide_followers", "link": "decide_followers",
+            "expand_level": "expand", "complete": "expand"}
 
 
 def clue_last_launch_count(ctx) -> int:
@@ -372,8 +381,20 @@ class Clusterer:
     def set_profiling(self, on=True):
         _check(clue_set_profiling(self.ctx, on), "clue_set_profiling", self.ctx)
 
+    def kernel_times(self):
+        """{kernel: ms} of the last profiled run (repeated launches summed)."""
+        out = {}
+        for k, v in clue_stage_times(self.ctx):
+            out[k] = out.get(k, 0.0) + v
+        return out
+
     def stage_times(self):
-        return clue_stage_times(self.ctx)
+        """{pipeline step: ms} of the last profiled run."""
+        out = {}
+        for k, v in clue_stage_times(self.ctx):
+            st = STAGE_OF.get(k, k)
+            out[st] = out.get(st, 0.0) + v
+        return out
 
     def launch_count(self):
         return clue_last_launch_count(self.ctx)

@@ -27,7 +27,7 @@ namespace {
 
 constexpr int NCLASS = 5;
 constexpr int64_t CLASS_EDGE[NCLASS + 1] = {0, 32768, 100000, 316228, 1000000, INT64_MAX};
-constexpr int NSTAGE_EVENTS = 6;
+constexpr int NPROF = 40;  // profiling events: one before the first kernel, one after each group
 constexpr int NSTAGING = 4;
 constexpr size_t GRAPH_CACHE_MAX = 16;
 constexpr int64_t MAX_HITS = 2147483646LL;
@@ -91,7 +91,8 @@ struct clue_ctx {
     int block_density = 256;
     bool profiling = false;
     bool prof_recorded = false;
-    cudaEvent_t pev[NSTAGE_EVENTS] = {};
+    cudaEvent_t pev[NPROF] = {};
+    std::vector<const char *> prof_names;  // name of the kernel(s) ending at pev[i + 1]
     Buffers last{};
     LaunchCfg last_cfg{};
     bool have_last = false;
@@ -206,25 +207,31 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     };
     const size_t n = (size_t)N, c = (size_t)C;
     b.key = (int32_t *)take(n * 4);
+    b.rank = (int32_t *)take(n * 4);
     b.count = (int32_t *)take(c * 4);
     b.cell_start = (int32_t *)take((c + 1) * 4);
     b.perm = (int32_t *)take(n * 4);
     b.tmp = (int32_t *)take(n * 4);
     b.big = (int32_t *)take((n / SMALL_SEGMENT + 1) * 4);
-    b.ids_s = (int32_t *)take(n * 4);
-    b.xs = (float *)take(n * 4);
-    b.ys = (float *)take(n * 4);
-    b.ws = (float *)take(n * 4);
+    b.sp = (float4 *)take(n * 16);
     b.lay_s = (int32_t *)take(n * 4);
-    b.rho_s = (float *)take(n * 4);
-    b.rho = (float *)take(n * 4);
-    b.delta2 = (float *)take(n * 4);
-    b.nh = (int32_t *)take(n * 4);
+    // one 16-byte-per-hit region: the grid fill's slot records, then (after
+    // the fill) rho in sorted order, rho, delta^2 and nh by hit
+    b.rec = (float4 *)take(n * 16);
+    if (!dry) {
+        b.rho_s = (float *)b.rec;
+        b.rho = b.rho_s + n;
+        b.delta2 = b.rho + n;
+        b.nh = (int32_t *)(b.delta2 + n);
+    }
     b.flags = (uint8_t *)take(n);
     b.fcount = (int32_t *)take(n * 4);
     b.hs = (unsigned long long *)take((n + 1) * 8);
     b.fol = (int32_t *)take(n * 4);
     b.seed_list = (int32_t *)take(n * 4);
+    b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
+    b.front_a = b.perm;  // the frontiers reuse the grid fill's scratch
+    b.front_b = b.tmp;
     const int64_t parts = std::max(scan_partials_needed(N), scan_partials_needed(C)) + 1;
     b.scan_partials = take((size_t)parts * 8);
     b.scan_partials_cap = parts;
@@ -311,6 +318,8 @@ LaunchCfg make_cfg(const clue_ctx *ctx) {
 }
 
 // Queue the whole pipeline (S1 grid fill .. S5 expansion) on ctx->stream.
+// With profiling on, an event is recorded before the first kernel and after
+// each launch group, named in ctx->prof_names.
 int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &cfg,
             int *launches) {
     cudaStream_t s = ctx->stream;
@@ -322,30 +331,44 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(cudaStreamIsCapturing(s, &cap));
     const unsigned rec_flags =
         cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-#define REC(i) CK(cudaEventRecordWithFlags(ctx->pev[i], s, rec_flags))
-    CK(cudaMemsetAsync(&b.ctrl->overflow, 0, 2 * sizeof(unsigned), s));
+    int ev = 0;
+    ctx->prof_names.clear();
+    auto rec = [&](const char *name) -> cudaError_t {
+        if (!prof) return cudaSuccess;
+        if (name) ctx->prof_names.push_back(name);
+        return cudaEventRecordWithFlags(ctx->pev[ev++], s, rec_flags);
+    };
+    CK(cudaMemsetAsync(&b.ctrl->overflow, 0, sizeof(Ctrl) - sizeof(unsigned), s));
     CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
-    if (prof) REC(0);
+    CK(rec(nullptr));
     CK(launch_fill_count(b, p, cfg, s));
+    CK(rec("fill_count"));
     CK(launch_scan_cells(b, cfg, s, &nl));
+    CK(rec("scan_cells"));
     CK(launch_fill_scatter(b, cfg, s));
+    CK(rec("fill_scatter"));
     CK(launch_fill_canon(b, cfg, s));
+    CK(rec("fill_canon"));
     CK(launch_fill_big(b, cfg, s));
+    CK(rec("fill_big"));
     nl += 4;
-    if (prof) REC(1);
     CK(launch_rho(b, p, cfg, s));
-    if (prof) REC(2);
+    CK(rec("rho"));
     CK(launch_nh(b, p, cfg, s));
-    if (prof) REC(3);
+    CK(rec("nh_delta"));
     CK(launch_decide(b, p, cfg, s));
+    CK(rec("decide"));
     CK(launch_scan_hits(b, cfg, s, &nl));
+    CK(rec("scan_hits"));
     CK(launch_link(b, cfg, s));
-    if (prof) REC(4);
-    CK(launch_expand(b, cfg, s));
+    CK(rec("link"));
+    for (int level = 0; level < EXPAND_LEVELS; ++level) {
+        CK(launch_expand_level(b, cfg, level, s));
+        CK(rec("expand_level"));
+    }
     CK(launch_complete(b, cfg, s));
-    if (prof) REC(5);
-    nl += 6;
-#undef REC
+    CK(rec("complete"));
+    nl += 5 + EXPAND_LEVELS;
     *launches = nl;
     return CLUE_OK;
 }
@@ -505,7 +528,7 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
     if (!std::isfinite(o.x_min) || !std::isfinite(o.x_max) || !std::isfinite(o.y_min) ||
         !std::isfinite(o.y_max) || !(o.x_max > o.x_min) || !(o.y_max > o.y_min) ||
         o.max_layers < 1 || !(o.bin_size >= 0.0f) || !std::isfinite(o.bin_size) ||
-        o.block_size < 0 || o.block_size > 512 || (o.block_size % 32) != 0)
+        o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
         return CLUE_ERR_ARG;
     clue_ctx *ctx = new (std::nothrow) clue_ctx();
     if (!ctx) return CLUE_ERR_OOM;
@@ -539,7 +562,7 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
         e = cudaEventCreateWithFlags(&ctx->staging[i].done, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail(e, "cudaEventCreate");
     }
-    for (int i = 0; i < NSTAGE_EVENTS; ++i) {
+    for (int i = 0; i < NPROF; ++i) {
         e = cudaEventCreate(&ctx->pev[i]);
         if (e != cudaSuccess) return fail(e, "cudaEventCreate");
     }
@@ -612,17 +635,15 @@ int clue_sync(clue_ctx *ctx) {
     return CLUE_OK;
 }
 
-int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
-                        const float *energy, const int64_t *offsets, int32_t n_events,
-                        float dc, float rhoc, float delta_c, float delta_o,
-                        int32_t *cluster_id, uint8_t *is_seed) {
-    if (!ctx || n_events < 0 || (n_events > 0 && !offsets)) return CLUE_ERR_ARG;
-    if (n_events == 0) return CLUE_OK;
-    const int64_t N = offsets[n_events];
-    if (N < 0 || N > MAX_HITS) return CLUE_ERR_ARG;
-    if (N == 0) return check_params(dc, rhoc, delta_c, delta_o);
-    if (!x || !y || !layer || !energy || !cluster_id || !is_seed) return CLUE_ERR_ARG;
-    CK(cudaSetDevice(ctx->device));
+namespace {
+struct HostIO {
+    float *x, *y, *e;
+    int32_t *l, *cid;
+    uint8_t *seed;
+};
+
+// Context-owned device buffers for n hits of inputs and outputs (grow-only).
+int ensure_hio(clue_ctx *ctx, int64_t N, HostIO &io) {
     const size_t n = (size_t)N;
     const size_t need = 5 * align_up(n * 4) + align_up(n);
     if (need > ctx->hio_cap) {
@@ -636,12 +657,34 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
         ctx->hio_cap = cap;
     }
     char *p = ctx->hio;
-    float *dx = (float *)p;
-    float *dy = (float *)(p + align_up(n * 4));
-    int32_t *dl = (int32_t *)(p + 2 * align_up(n * 4));
-    float *de = (float *)(p + 3 * align_up(n * 4));
-    int32_t *dc_out = (int32_t *)(p + 4 * align_up(n * 4));
-    uint8_t *ds = (uint8_t *)(p + 5 * align_up(n * 4));
+    io.x = (float *)p;
+    io.y = (float *)(p + align_up(n * 4));
+    io.l = (int32_t *)(p + 2 * align_up(n * 4));
+    io.e = (float *)(p + 3 * align_up(n * 4));
+    io.cid = (int32_t *)(p + 4 * align_up(n * 4));
+    io.seed = (uint8_t *)(p + 5 * align_up(n * 4));
+    return CLUE_OK;
+}
+}  // namespace
+
+int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
+                        const float *energy, const int64_t *offsets, int32_t n_events,
+                        float dc, float rhoc, float delta_c, float delta_o,
+                        int32_t *cluster_id, uint8_t *is_seed) {
+    if (!ctx || n_events < 0 || (n_events > 0 && !offsets)) return CLUE_ERR_ARG;
+    if (n_events == 0) return CLUE_OK;
+    const int64_t N = offsets[n_events];
+    if (N < 0 || N > MAX_HITS) return CLUE_ERR_ARG;
+    if (N == 0) return check_params(dc, rhoc, delta_c, delta_o);
+    if (!x || !y || !layer || !energy || !cluster_id || !is_seed) return CLUE_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const size_t n = (size_t)N;
+    HostIO io;
+    int rc0 = ensure_hio(ctx, N, io);
+    if (rc0) return rc0;
+    float *dx = io.x, *dy = io.y, *de = io.e;
+    int32_t *dl = io.l, *dc_out = io.cid;
+    uint8_t *ds = io.seed;
     cudaStream_t s = ctx->stream;
     CK(cudaMemcpyAsync(dx, x, n * 4, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dy, y, n * 4, cudaMemcpyHostToDevice, s));
@@ -673,15 +716,19 @@ int clue_set_profiling(clue_ctx *ctx, int32_t on) {
 
 int clue_stage_times(clue_ctx *ctx, float *ms, int32_t cap, char *names, int64_t names_cap) {
     if (!ctx || (cap > 0 && !ms)) return -CLUE_ERR_ARG;
-    static const char kNames[] = "grid_fill,rho,nh_delta,decide_followers,expand";
+    if (!ctx->prof_recorded || ctx->prof_names.empty()) return -CLUE_ERR_STATE;
+    const int n = (int)ctx->prof_names.size();
     if (names && names_cap > 0) {
-        std::strncpy(names, kNames, (size_t)names_cap - 1);
+        std::string all;
+        for (int i = 0; i < n; ++i) {
+            if (i) all += ",";
+            all += ctx->prof_names[i];
+        }
+        std::strncpy(names, all.c_str(), (size_t)names_cap - 1);
         names[names_cap - 1] = 0;
     }
-    if (!ctx->prof_recorded) return -CLUE_ERR_STATE;
-    cudaError_t e = cudaEventSynchronize(ctx->pev[NSTAGE_EVENTS - 1]);
+    cudaError_t e = cudaEventSynchronize(ctx->pev[n]);
     if (e != cudaSuccess) return -cuda_fail(ctx, e, "cudaEventSynchronize");
-    const int n = NSTAGE_EVENTS - 1;
     for (int i = 0; i < n && i < cap; ++i) {
         e = cudaEventElapsedTime(&ms[i], ctx->pev[i], ctx->pev[i + 1]);
         if (e != cudaSuccess) return -cuda_fail(ctx, e, "cudaEventElapsedTime");
@@ -702,23 +749,26 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
     if (!ctx || reps < 1 || n_events < 1 || !offsets) return CLUE_ERR_ARG;
     int rc = check_params(dc, rhoc, delta_c, delta_o);
     if (rc) return rc;
+    for (int32_t e = 0; e < n_events; ++e)
+        if (offsets[e + 1] < offsets[e] || offsets[0] != 0) return CLUE_ERR_ARG;
+    if (offsets[n_events] > MAX_HITS) return CLUE_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
-    bool present[NCLASS] = {};
-    for (int32_t e = 0; e < n_events; ++e) present[class_of(offsets[e + 1] - offsets[e])] = true;
     cudaEvent_t t0, t1;
     CK(cudaEventCreate(&t0));
     CK(cudaEventCreate(&t1));
     const bool prof = ctx->profiling;
     ctx->profiling = false;
-    auto time_run = [&](float *out_ms) -> int {
-        // one untimed run (plans, arena growth), then `reps` timed ones
-        int r = run_batch(ctx, x, y, layer, energy, offsets, n_events, dc, rhoc, delta_c,
-                          delta_o, cluster_id, is_seed, false);
+    // time `reps` runs of a batch after one untimed run (plan, arena growth)
+    auto time_run = [&](const float *bx, const float *by, const int32_t *bl, const float *be,
+                        const int64_t *offs, int32_t ne, int32_t *bc, uint8_t *bs,
+                        float *out_ms) -> int {
+        int r = run_batch(ctx, bx, by, bl, be, offs, ne, dc, rhoc, delta_c, delta_o, bc, bs,
+                          false);
         if (r) return r;
         cudaError_t e = cudaEventRecord(t0, ctx->stream);
         for (int i = 0; i < reps && r == CLUE_OK && e == cudaSuccess; ++i)
-            r = run_batch(ctx, x, y, layer, energy, offsets, n_events, dc, rhoc, delta_c,
-                          delta_o, cluster_id, is_seed, false);
+            r = run_batch(ctx, bx, by, bl, be, offs, ne, dc, rhoc, delta_c, delta_o, bc, bs,
+                          false);
         if (r) return r;
         if (e == cudaSuccess) e = cudaEventRecord(t1, ctx->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -726,23 +776,47 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
         if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune timing");
         return clue_sync(ctx);
     };
-    const float scales[] = {1.0f, 1.5f, 2.0f, 3.0f, 4.0f};
-    const int blocks[] = {128, 256, 512};
+    const float scales[] = {1.0f, 1.5f, 2.0f, 3.0f, 4.0f, 6.0f};
+    const int blocks[] = {128, 256};
     const float user_bin = ctx->opts.bin_size;
     const int user_block = ctx->opts.block_size;
     ctx->opts.bin_size = 0.0f;
     ctx->opts.block_size = 0;
+    // Each size class is timed on its own events, copied into one contiguous
+    // sub-batch, so its bin size is chosen on its own time alone.
     for (int k = 0; k < NCLASS && rc == CLUE_OK; ++k) {
-        if (!present[k]) continue;
+        std::vector<int64_t> sub{0};
+        for (int32_t e = 0; e < n_events; ++e) {
+            const int64_t n = offsets[e + 1] - offsets[e];
+            if (n > 0 && class_of(n) == k) sub.push_back(sub.back() + n);
+        }
+        if (sub.size() < 2) continue;
+        HostIO io;
+        rc = ensure_hio(ctx, sub.back(), io);
+        if (rc) break;
+        int64_t at = 0;
+        for (int32_t e = 0; e < n_events && rc == CLUE_OK; ++e) {
+            const int64_t n = offsets[e + 1] - offsets[e];
+            if (n <= 0 || class_of(n) != k) continue;
+            const int64_t o = offsets[e];
+            cudaError_t ce = cudaMemcpyAsync(io.x + at, x + o, n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(io.y + at, y + o, n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(io.l + at, layer + o, n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(io.e + at, energy + o, n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+            if (ce != cudaSuccess) rc = cuda_fail(ctx, ce, "autotune gather");
+            at += n;
+        }
+        if (rc) break;
         float best = 1e30f, best_s = ctx->bin_scale[k];
-        for (float s : scales) {
-            ctx->bin_scale[k] = s;
+        for (float sc : scales) {
+            ctx->bin_scale[k] = sc;
             float ms = 0;
-            rc = time_run(&ms);
+            rc = time_run(io.x, io.y, io.l, io.e, sub.data(), (int32_t)sub.size() - 1, io.cid,
+                          io.seed, &ms);
             if (rc) break;
             if (ms < best) {
                 best = ms;
-                best_s = s;
+                best_s = sc;
             }
         }
         ctx->bin_scale[k] = best_s;
@@ -753,7 +827,7 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
         for (int bsz : blocks) {
             ctx->block_density = bsz;
             float ms = 0;
-            rc = time_run(&ms);
+            rc = time_run(x, y, layer, energy, offsets, n_events, cluster_id, is_seed, &ms);
             if (rc) break;
             if (ms < best) {
                 best = ms;
@@ -811,7 +885,7 @@ int clue_set_tuning(clue_ctx *ctx, const char *text) {
             if (k < 0 || !(sc >= 0.25f && sc <= 64.0f)) return CLUE_ERR_ARG;
             scale[k] = sc;
         } else if (std::sscanf(line.c_str(), "block %d %c", &bl, &tail) == 1) {
-            if (bl < 32 || bl > 512 || bl % 32) return CLUE_ERR_ARG;
+            if (bl < 32 || bl > 256 || bl % 32) return CLUE_ERR_ARG;
             block = bl;
         } else {
             return CLUE_ERR_ARG;

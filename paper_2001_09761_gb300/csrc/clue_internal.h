@@ -14,9 +14,6 @@ constexpr int TILE = 1024;
 // per-slot ranking.
 constexpr int SMALL_SEGMENT = 128;
 
-// Per-warp queue capacity of the frontier expansion (node ids).
-constexpr int EXPAND_QCAP = 512;
-
 // cluster id of a follower whose id has not been passed down yet.
 constexpr int32_t PENDING = -2;
 
@@ -44,12 +41,17 @@ struct Tile {
     int32_t pad;
 };
 
-// Device control block: zeroed at the start of every run.
+// Levels of the frontier expansion run as separate launches; a tree deeper
+// than this is finished by the completion pass.
+constexpr int EXPAND_LEVELS = 12;
+
+// Device control block.  `err` is sticky until clue_sync reads it; the rest
+// is zeroed at the start of every run.
 struct Ctrl {
     unsigned err;        // ERRBIT_* raised by any kernel
-    unsigned overflow;   // an expansion queue overflowed
+    unsigned overflow;   // the expansion left nodes for the completion pass
     int32_t nbig;        // cell segments queued for the CTA sorter
-    int32_t pad;
+    int32_t fsize[3];    // frontier sizes, rotating over the expansion levels
 };
 
 // Runtime parameters of one run (all events share them).
@@ -80,13 +82,15 @@ struct Buffers {
     int64_t C;      // total cells
     // grid
     int32_t *key;        // [N] local cell of hit
+    int32_t *rank;       // [N] arrival rank of the hit in its cell (from the count)
     int32_t *count;      // [C] hits per cell (zeroed per run)
     int32_t *cell_start; // [C + 1]
-    int32_t *perm;       // [N] hit ids grouped by cell, unordered within a cell
+    float4 *rec;         // [N] hits grouped by cell, unordered within a cell:
+                         //     x, y, w, id (int bits); aliases rho_s..nh
+    int32_t *perm;       // [N] scratch of the CTA sorter
     int32_t *tmp;        // [N] scratch for the CTA sorter
     int32_t *big;        // [N / SMALL_SEGMENT + 1] cells queued for the CTA sorter
-    int32_t *ids_s;      // [N] hit ids sorted by (cell, id)
-    float *xs, *ys, *ws; // [N] coordinates and weights in sorted order
+    float4 *sp;          // [N] hits sorted by (cell, id): x, y, w, id (int bits)
     int32_t *lay_s;      // [N] layer in sorted order
     // density
     float *rho_s;        // [N] rho in sorted order
@@ -96,9 +100,12 @@ struct Buffers {
     // decision / expansion
     uint8_t *flags;      // [N]
     int32_t *fcount;     // [N] followers per hit (zeroed in the fill step)
+    int32_t *frank;      // [N] arrival rank of a follower in its nh's list (aliases rank)
     unsigned long long *hs;  // [N + 1] exclusive scan of (seed << 32 | followers)
     int32_t *fol;        // [N] follower lists (CSR by nh)
     int32_t *seed_list;  // [N] seeds by global seed rank
+    int32_t *front_a;    // [N] expansion frontiers (alias perm / tmp, free after S1)
+    int32_t *front_b;
     // scan scratch
     void *scan_partials; // [nblocks + 1] block sums
     int64_t scan_partials_cap;
@@ -123,7 +130,8 @@ cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cud
 cudaError_t launch_decide(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
 cudaError_t launch_link(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);  // all levels
+cudaError_t launch_expand_level(const Buffers &b, const LaunchCfg &c, int level, cudaStream_t s);
 cudaError_t launch_complete(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_export(const Buffers &b, const LaunchCfg &c, float *rho, float *delta,
                           int32_t *nh, cudaStream_t s);

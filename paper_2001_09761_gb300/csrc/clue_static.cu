@@ -36,10 +36,10 @@ constexpr size_t NB = (size_t)STATIC_MAX_HITS, CB = (size_t)STATIC_MAX_CELLS;
 // Byte layout of the scratch array (offsets in order of the Buffers fields).
 constexpr size_t STATIC_BYTES =
     al(sizeof(Ctrl)) + al(sizeof(EventDesc)) + al(STATIC_MAX_TILES * sizeof(Tile)) +
-    al(NB * 4) /*key*/ + al(CB * 4) /*count*/ + al((CB + 1) * 4) /*cell_start*/ +
+    al(NB * 4) /*key*/ + al(NB * 4) /*rank*/ + al(CB * 4) /*count*/ + al((CB + 1) * 4) /*cell_start*/ +
     al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ + al((NB / SMALL_SEGMENT + 1) * 4) /*big*/ +
-    al(NB * 4) /*ids_s*/ + 3 * al(NB * 4) /*xs ys ws*/ + al(NB * 4) /*lay_s*/ +
-    al(NB * 4) /*rho_s*/ + al(NB * 4) /*rho*/ + al(NB * 4) /*delta2*/ + al(NB * 4) /*nh*/ +
+    al(NB * 16) /*sp*/ + al(NB * 4) /*lay_s*/ +
+    al(NB * 16) /*rec = rho_s, rho, delta2, nh*/ +
     al(NB) /*flags*/ + al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
     al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/;
 
@@ -130,25 +130,27 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     EventDesc *d_ev = (EventDesc *)take(sizeof(EventDesc));
     Tile *d_tiles = (Tile *)take(STATIC_MAX_TILES * sizeof(Tile));
     b.key = (int32_t *)take(NB * 4);
+    b.rank = (int32_t *)take(NB * 4);
     b.count = (int32_t *)take(CB * 4);
     b.cell_start = (int32_t *)take((CB + 1) * 4);
     b.perm = (int32_t *)take(NB * 4);
     b.tmp = (int32_t *)take(NB * 4);
     b.big = (int32_t *)take((NB / SMALL_SEGMENT + 1) * 4);
-    b.ids_s = (int32_t *)take(NB * 4);
-    b.xs = (float *)take(NB * 4);
-    b.ys = (float *)take(NB * 4);
-    b.ws = (float *)take(NB * 4);
+    b.sp = (float4 *)take(NB * 16);
     b.lay_s = (int32_t *)take(NB * 4);
-    b.rho_s = (float *)take(NB * 4);
-    b.rho = (float *)take(NB * 4);
-    b.delta2 = (float *)take(NB * 4);
-    b.nh = (int32_t *)take(NB * 4);
+    b.rec = (float4 *)take(NB * 16);
+    b.rho_s = (float *)b.rec;
+    b.rho = b.rho_s + NB;
+    b.delta2 = b.rho + NB;
+    b.nh = (int32_t *)(b.delta2 + NB);
     b.flags = (uint8_t *)take(NB);
     b.fcount = (int32_t *)take(NB * 4);
     b.hs = (unsigned long long *)take((NB + 1) * 8);
     b.fol = (int32_t *)take(NB * 4);
     b.seed_list = (int32_t *)take(NB * 4);
+    b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
+    b.front_a = b.perm;
+    b.front_b = b.tmp;
     b.scan_partials = take((size_t)STATIC_PARTS * 8);
     b.scan_partials_cap = STATIC_PARTS;
     if ((size_t)(p - (char *)base) > STATIC_BYTES) return CLUE_ERR_STATE;

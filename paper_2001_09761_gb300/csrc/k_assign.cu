@@ -5,8 +5,8 @@
 // of Sec. 3), so seed numbering depends on thread timing.  Here seed ids are
 // ranks from a prefix sum over hit order, giving Algorithm 3's k++ numbering
 // (ascending seed index per event), and the follower lists are a CSR built by
-// the same prefix sum.  Expansion is k-way parallel as in the paper, one warp
-// per seed walking its follower tree breadth-first with a shared-memory queue.
+// the same prefix sum.  Expansion is k-way parallel as in the paper, one launch
+// per level of the frontier over all seeds' follower trees at once.
 #include <climits>
 
 #include "scan.cuh"
@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256) k_decide(Buffers b, Params p) {
             const bool outl = (r < p.rhoc) && (d2 > p.dos2);
             const bool fol = !seed && !outl && j >= 0;
             b.flags[g] = (seed ? F_SEED : 0) | (outl ? F_OUTLIER : 0) | (fol ? F_FOLLOWER : 0);
-            if (fol) atomicAdd(&b.fcount[j], 1);
+            if (fol) b.frank[g] = atomicAdd(&b.fcount[j], 1);
         }
     }
 }
@@ -51,32 +51,47 @@ cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t 
                                               s, launches);
 }
 
-// Seeds take their per-event id and enter the seed list; followers enter the
-// CSR list of their nearest-higher (order inside a list is irrelevant: each
-// follower has exactly one parent); everything else is noise for now.
+// Seeds take their per-event id; seeds with followers enter the first
+// frontier of the expansion (one atomic per CTA); followers enter the CSR list
+// of their nearest-higher at the rank the decision step's count returned
+// (order inside a list is irrelevant: each follower has exactly one parent);
+// everything else is noise for now.
 __global__ void __launch_bounds__(256) k_link(Buffers b) {
+    __shared__ int ws[32];
+    __shared__ int s_base;
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int64_t hoff = b.events[tl.event].hit_off;
         const unsigned ebase = (unsigned)(b.hs[hoff] >> 32);
-        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-            const int g = tl.start + k;
-            const uint8_t f = b.flags[g];
-            if (f & F_SEED) {
-                const unsigned srank = (unsigned)(b.hs[g] >> 32);
-                b.cid[g] = (int32_t)(srank - ebase);
-                b.seed_list[srank] = g;
-                b.is_seed[g] = 1;
-            } else {
-                b.is_seed[g] = 0;
-                if (f & F_FOLLOWER) {
-                    const int j = b.nh[g];
-                    const int slot = (int)(unsigned)b.hs[j] + atomicSub(&b.fcount[j], 1) - 1;
-                    b.fol[slot] = g;
-                    b.cid[g] = PENDING;
+        for (int k0 = 0; k0 < tl.len; k0 += blockDim.x) {
+            const int k = k0 + threadIdx.x;
+            int root = 0;
+            if (k < tl.len) {
+                const int g = tl.start + k;
+                const uint8_t f = b.flags[g];
+                if (f & F_SEED) {
+                    const unsigned long long hg = b.hs[g];
+                    b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);
+                    b.is_seed[g] = 1;
+                    root = (unsigned)b.hs[g + 1] != (unsigned)hg;  // has followers
                 } else {
-                    b.cid[g] = -1;
+                    b.is_seed[g] = 0;
+                    if (f & F_FOLLOWER) {
+                        const int j = b.nh[g];
+                        b.fol[(int)(unsigned)b.hs[j] + b.frank[g]] = g;
+                        b.cid[g] = PENDING;
+                    } else {
+                        b.cid[g] = -1;
+                    }
                 }
+            }
+            int n_root;
+            const int r = block_incl_scan(root, ws, &n_root) - root;
+            if (n_root) {
+                if (threadIdx.x == 0) s_base = atomicAdd(&b.ctrl->fsize[0], n_root);
+                __syncthreads();
+                if (root) b.seed_list[s_base + r] = tl.start + k;
+                __syncthreads();
             }
         }
     }
@@ -88,86 +103,94 @@ cudaError_t launch_link(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One warp per seed (grid-stride over the seed list).  The warp dequeues up to
-// 32 nodes, scans their follower counts, and hands out the followers across
-// its lanes (each lane finds the node owning its follower by bisection over
-// the scanned counts), so a node with many followers does not serialise one
-// lane.  A tree whose frontier outgrows the queue is left partly pending and
-// finished by k_complete.
+// Frontier expansion down the follower forest, all seeds of the batch at once
+// (k-way parallel at the first level, as in the paper).  Level 0 is the list
+// of seeds that have followers; each level hands every frontier node's id to
+// its followers and puts
+// the followers that have followers of their own into the next frontier.  A
+// CTA takes 256 frontier nodes, scans their follower counts, and spreads the
+// followers over its threads (each finds its owner node by bisection of the
+// scanned counts), so a node with many followers is not left to one thread.
+// Appends to the next frontier take one atomic per CTA round (block scan).
+// Levels past EXPAND_LEVELS are left to the completion pass.
 constexpr int EXPAND_THREADS = 256;
-constexpr int EXPAND_WARPS = EXPAND_THREADS / 32;
 
-__global__ void __launch_bounds__(EXPAND_THREADS) k_expand(Buffers b) {
-    __shared__ int queue[EXPAND_WARPS][EXPAND_QCAP];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int *q = queue[warp];
-    const int nseeds = (int)(b.hs[b.N] >> 32);
-    const int nwarps = gridDim.x * EXPAND_WARPS;
-    bool ovf = false;
-    for (int si = blockIdx.x * EXPAND_WARPS + warp; si < nseeds; si += nwarps) {
-        const int root = b.seed_list[si];
-        const int id = b.cid[root];
-        if (lane == 0) q[0] = root;
-        __syncwarp();
-        int head = 0, tail = 1;
-        int64_t dequeued = 0;  // a tree holds at most N nodes: bounds the walk
-        while (head < tail) {
-            const int cnt = min(32, tail - head);
-            dequeued += cnt;
-            if (dequeued > b.N) {
-                if (lane == 0) atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
-                break;
-            }
-            int a = 0, c = 0;
-            if (lane < cnt) {
-                const int node = q[(head + lane) & (EXPAND_QCAP - 1)];
-                a = (int)(unsigned)b.hs[node];
-                c = (int)(unsigned)b.hs[node + 1] - a;
-            }
-            const int incl = warp_incl_scan(c);
-            const int total = __shfl_sync(FULL_MASK, incl, 31);
-            const int excl = incl - c;
-            head += cnt;
-            if (tail - head + total > EXPAND_QCAP) {
-                ovf = true;
-                break;
-            }
-            for (int base = 0; base < total; base += 32) {
-                const int u = base + lane;
-                int lo = 0, hi = 31;
-#pragma unroll
-                for (int it = 0; it < 5; ++it) {
-                    const int mid = (lo + hi) >> 1;
-                    if (__shfl_sync(FULL_MASK, incl, mid) > u) hi = mid; else lo = mid + 1;
-                }
-                const int ao = __shfl_sync(FULL_MASK, a, lo);
-                const int eo = __shfl_sync(FULL_MASK, excl, lo);
-                if (u < total) {
-                    const int child = b.fol[ao + (u - eo)];
-                    b.cid[child] = id;
-                    q[(tail + u) & (EXPAND_QCAP - 1)] = child;
-                }
-            }
-            tail += total;
-            __syncwarp();
+__global__ void __launch_bounds__(EXPAND_THREADS) k_expand_level(Buffers b, int level) {
+    __shared__ int s_off[EXPAND_THREADS + 1];
+    __shared__ int s_a[EXPAND_THREADS];
+    __shared__ int s_id[EXPAND_THREADS];
+    __shared__ int ws[32];
+    __shared__ int s_base;
+    const int tid = threadIdx.x;
+    const int *in = level == 0 ? b.seed_list : ((level & 1) ? b.front_a : b.front_b);
+    int *out = (level & 1) ? b.front_b : b.front_a;
+    const int n_in = b.ctrl->fsize[level % 3];
+    int *out_size = &b.ctrl->fsize[(level + 1) % 3];
+    if (blockIdx.x == 0 && tid == 0) b.ctrl->fsize[(level + 2) % 3] = 0;  // next level's output
+    for (int base = blockIdx.x * EXPAND_THREADS; base < n_in; base += gridDim.x * EXPAND_THREADS) {
+        const int i = base + tid;
+        int a = 0, c = 0, id = 0;
+        if (i < n_in) {
+            const int node = in[i];
+            a = (int)(unsigned)b.hs[node];
+            c = (int)(unsigned)b.hs[node + 1] - a;
+            id = b.cid[node];
         }
-        __syncwarp();
+        int total;
+        const int incl = block_incl_scan(c, ws, &total);
+        s_off[tid] = incl - c;
+        s_a[tid] = a;
+        s_id[tid] = id;
+        if (tid == 0) s_off[EXPAND_THREADS] = total;
+        __syncthreads();
+        for (int u0 = 0; u0 < total; u0 += EXPAND_THREADS) {
+            const int u = u0 + tid;
+            int child = 0, inner = 0;
+            if (u < total) {
+                int lo = 0, hi = EXPAND_THREADS - 1;  // last owner with s_off <= u
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
+                }
+                child = b.fol[s_a[lo] + (u - s_off[lo])];
+                b.cid[child] = s_id[lo];
+                inner = (unsigned)b.hs[child + 1] != (unsigned)b.hs[child];
+            }
+            // one append per CTA round: scan the inner flags, one atomic
+            int n_inner;
+            const int rank = block_incl_scan(inner, ws, &n_inner) - inner;
+            if (n_inner) {
+                if (tid == 0) s_base = atomicAdd(out_size, n_inner);
+                __syncthreads();
+                if (inner) out[s_base + rank] = child;
+                __syncthreads();
+            }
+        }
+        __syncthreads();
     }
-    if (ovf && lane == 0) atomicOr(&b.ctrl->overflow, 1u);
 }
 
-cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
-    k_expand<<<c.grid_cap > 0 ? c.grid_cap : 1, EXPAND_THREADS, 0, s>>>(b);
+cudaError_t launch_expand_level(const Buffers &b, const LaunchCfg &c, int level, cudaStream_t s) {
+    k_expand_level<<<c.grid_cap > 0 ? c.grid_cap : 1, EXPAND_THREADS, 0, s>>>(b, level);
     return cudaGetLastError();
 }
 
+cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
+    for (int level = 0; level < EXPAND_LEVELS; ++level) {
+        cudaError_t e = launch_expand_level(b, c, level, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // Pending followers left after the expansion are noise (their chain ends at an
-// outlier or at a hit with no nearest-higher) unless a queue overflowed; then
+// outlier or at a hit with no nearest-higher) unless the expansion stopped
+// with a non-empty frontier (a tree deeper than EXPAND_LEVELS); then
 // each pending hit follows its nh chain to the first hit with a final id (a
 // seed, an expanded follower, or noise).  The chain is finite because rho
 // rises strictly along it; the walk is still bounded by N steps.
 __global__ void __launch_bounds__(256) k_complete(Buffers b) {
-    const bool ovf = b.ctrl->overflow != 0;
+    const bool ovf = b.ctrl->overflow != 0 || b.ctrl->fsize[EXPAND_LEVELS % 3] != 0;
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {

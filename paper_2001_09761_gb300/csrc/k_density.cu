@@ -4,13 +4,16 @@
 // One thread per hit in grid (sorted) order, so a warp covers neighbouring
 // cells and its window loads hit the same lines.  The window of Eq. 1 is the
 // set of bins met by [x +- R] x [y +- R]; bins of one grid row are adjacent in
-// the sorted arrays, so a window row is one contiguous run.
+// the sorted array, so a window row is one contiguous run.  Each sorted hit is
+// one float4 (x, y, w, id), so a candidate costs one 16-byte load.
 //
 // rho is summed in fp32 in ascending hit index j over N_dc(i) (the order is
 // part of the result's definition, independent of the bin size): every cell
-// lists its hits in ascending index, and the kernel merges the window cells'
-// lists with one cursor per cell, adding w_j for each j that passes the
-// distance test as the merge reaches it.
+// lists its hits in ascending index, and the kernel merges the lists of the
+// window's non-empty cells, adding w_j for each j that passes the distance
+// test as the merge reaches it.  With the bin at least 2 R wide a window has
+// at most 2 x 2 cells, merged by one loop that every lane of a warp runs
+// alike (lanes that take different code paths would run one after another).
 #include <climits>
 
 #include "device_common.cuh"
@@ -31,23 +34,28 @@ __device__ __forceinline__ Window window_of(float xi, float yi, float dr, const 
     return w;
 }
 
-// K-cursor merge over a window of at most KX x KY cells.  Cursor k follows
-// cell (ly + k / KX, lx + k % KX); cells outside the window are empty.
-template <int KX, int KY>
-__device__ __forceinline__ float rho_merge(const Buffers &b, int64_t plane, int nbx, const Window &w,
-                                           float xi, float yi, float dc2) {
-    constexpr int K = KX * KY;
-    int pos[K], end[K], head[K];
+__device__ __forceinline__ int id_of(const float4 &h) { return __float_as_int(h.w); }
+
+__device__ __forceinline__ float add_if_near(float r, float xi, float yi, const float4 &h,
+                                             float dc2) {
+    return sq_dist(xi, yi, h.x, h.y) < dc2 ? __fadd_rn(r, h.z) : r;
+}
+
+// Merge of up to K sorted cell lists given as [p[k], e[k]) (k < nk).  With
+// CACHE the head hit of every list stays in registers (one load per
+// candidate); without it only the head ids do (fewer registers, two loads).
+template <int K, bool CACHE>
+__device__ __forceinline__ float merge_k(const float4 *__restrict__ sp, int (&p)[K],
+                                         const int (&e)[K], int nk, float xi, float yi,
+                                         float dc2) {
+    float4 h[CACHE ? K : 1];
+    int head[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int cx = k % KX, cy = k / KX;
-        const bool in = (w.lx + cx <= w.hx) && (w.ly + cy <= w.hy);
-        const int64_t c = plane + (int64_t)(w.ly + cy) * nbx + (w.lx + cx);
-        const int a = in ? b.cell_start[c] : 0;
-        const int e = in ? b.cell_start[c + 1] : 0;
-        pos[k] = a;
-        end[k] = e;
-        head[k] = a < e ? b.ids_s[a] : INT_MAX;
+        const bool live = k < nk && p[k] < e[k];
+        const float4 v = live ? sp[p[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (CACHE) h[k] = v;
+        head[k] = live ? id_of(v) : INT_MAX;
     }
     float r = 0.0f;
     while (true) {
@@ -59,30 +67,57 @@ __device__ __forceinline__ float rho_merge(const Buffers &b, int64_t plane, int 
                 am = k;
             }
         if (m == INT_MAX) break;
-        int q = pos[0], qe = end[0];
-#pragma unroll
-        for (int k = 1; k < K; ++k)
-            if (am == k) {
-                q = pos[k];
-                qe = end[k];
-            }
-        if (sq_dist(xi, yi, b.xs[q], b.ys[q]) < dc2) r = __fadd_rn(r, b.ws[q]);
-        ++q;
-        const int nxt = q < qe ? b.ids_s[q] : INT_MAX;
 #pragma unroll
         for (int k = 0; k < K; ++k)
             if (am == k) {
-                pos[k] = q;
-                head[k] = nxt;
+                const int q = p[k]++;
+                r = add_if_near(r, xi, yi, CACHE ? h[k] : sp[q], dc2);
+                const bool live = q + 1 < e[k];
+                if (CACHE) {
+                    h[k] = live ? sp[q + 1] : h[k];
+                    head[k] = live ? id_of(h[k]) : INT_MAX;
+                } else {
+                    head[k] = live ? id_of(sp[q + 1]) : INT_MAX;
+                }
             }
     }
     return r;
 }
 
+// Windows of at most 3 x 3 cells (a bin size between d_c and 2 d_c).
+__device__ __forceinline__ float rho_window9(const Buffers &b, int64_t plane, int nbx, const Window &w, float xi,
+                             float yi, float dc2) {
+    int p[9], e[9];
+    int nk = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        p[k] = e[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int cx = k % 3, cy = k / 3;
+        int a = 0, z = 0;
+        if ((w.lx + cx <= w.hx) && (w.ly + cy <= w.hy)) {
+            const int64_t c = plane + (int64_t)(w.ly + cy) * nbx + (w.lx + cx);
+            a = b.cell_start[c];
+            z = b.cell_start[c + 1];
+        }
+        const bool ne = a < z;
+#pragma unroll
+        for (int m = 0; m < 9; ++m)
+            if (ne && m == nk) {
+                p[m] = a;
+                e[m] = z;
+            }
+        nk += ne;
+    }
+    return merge_k<9, false>(b.sp, p, e, nk, xi, yi, dc2);
+}
+
 // Any window size: repeatedly take the smallest id above the last one taken.
 // Quadratic in the window population; used only when the window spans more
 // than 3 x 3 bins (a bin size near d_c plus rounding at a bin edge).
-__device__ float rho_select(const Buffers &b, int64_t plane, int nbx, const Window &w, float xi,
+__device__ __forceinline__ float rho_select(const Buffers &b, int64_t plane, int nbx, const Window &w, float xi,
                             float yi, float dc2) {
     float r = 0.0f;
     int last = -1;
@@ -93,7 +128,7 @@ __device__ float rho_select(const Buffers &b, int64_t plane, int nbx, const Wind
                 const int64_t c = plane + (int64_t)by * nbx + bx;
                 const int e = b.cell_start[c + 1];
                 for (int q = b.cell_start[c]; q < e; ++q) {
-                    const int j = b.ids_s[q];
+                    const int j = id_of(b.sp[q]);
                     if (j > last) {  // cells are ascending: the first one above `last`
                         if (j < best) {
                             best = j;
@@ -104,30 +139,75 @@ __device__ float rho_select(const Buffers &b, int64_t plane, int nbx, const Wind
                 }
             }
         if (bq < 0) break;
-        if (sq_dist(xi, yi, b.xs[bq], b.ys[bq]) < dc2) r = __fadd_rn(r, b.ws[bq]);
+        r = add_if_near(r, xi, yi, b.sp[bq], dc2);
         last = best;
     }
     return r;
 }
 
-__global__ void __launch_bounds__(512) k_rho(Buffers b, Params p) {
+// Windows of at most 2 x 2 cells.  Every lane runs the same loop (a lane
+// whose window has fewer cells just has empty cursors), so lanes of a warp
+// never take different code paths; a cursor keeps only its head id in a
+// register and the chosen candidate is loaded once.
+__device__ __forceinline__ float rho_window4(const Buffers &b, int64_t plane, int nbx,
+                                             const Window &w, float xi, float yi, float dc2) {
+    const float4 *__restrict__ sp = b.sp;
+    const int4 *__restrict__ spi = reinterpret_cast<const int4 *>(b.sp);  // id = .w
+    int p0, p1, p2, p3, e0, e1, e2, e3;
+    {
+        const int64_t r0 = plane + (int64_t)w.ly * nbx + w.lx;
+        const bool two_x = w.hx > w.lx, two_y = w.hy > w.ly;
+        p0 = b.cell_start[r0];
+        e0 = b.cell_start[r0 + 1];
+        p1 = e0;
+        e1 = two_x ? b.cell_start[r0 + 2] : e0;
+        const int64_t r1 = r0 + nbx;
+        p2 = two_y ? b.cell_start[r1] : 0;
+        e2 = two_y ? b.cell_start[r1 + 1] : 0;
+        p3 = e2;
+        e3 = (two_x && two_y) ? b.cell_start[r1 + 2] : e2;
+    }
+    int h0 = p0 < e0 ? spi[p0].w : INT_MAX;
+    int h1 = p1 < e1 ? spi[p1].w : INT_MAX;
+    int h2 = p2 < e2 ? spi[p2].w : INT_MAX;
+    int h3 = p3 < e3 ? spi[p3].w : INT_MAX;
+    float r = 0.0f;
+    while (true) {
+        const int m = min(min(h0, h1), min(h2, h3));
+        if (m == INT_MAX) break;
+        int q, e;
+        if (m == h0) { q = p0++; e = e0; }
+        else if (m == h1) { q = p1++; e = e1; }
+        else if (m == h2) { q = p2++; e = e2; }
+        else { q = p3++; e = e3; }
+        r = add_if_near(r, xi, yi, sp[q], dc2);
+        const int nx = q + 1 < e ? spi[q + 1].w : INT_MAX;
+        if (m == h0) h0 = nx;
+        else if (m == h1) h1 = nx;
+        else if (m == h2) h2 = nx;
+        else h3 = nx;
+    }
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_rho(Buffers b, Params p) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const EventDesc ev = b.events[tl.event];
         const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
-            const float xi = b.xs[q], yi = b.ys[q];
+            const float4 me = b.sp[q];
             const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
-            const Window w = window_of(xi, yi, p.rwin_rho, ev);
+            const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
             const int nx = w.hx - w.lx + 1, ny = w.hy - w.ly + 1;
             float r;
             if (nx <= 2 && ny <= 2)
-                r = rho_merge<2, 2>(b, plane, ev.nbx, w, xi, yi, p.dc2);
+                r = rho_window4(b, plane, ev.nbx, w, me.x, me.y, p.dc2);
             else if (nx <= 3 && ny <= 3)
-                r = rho_merge<3, 3>(b, plane, ev.nbx, w, xi, yi, p.dc2);
+                r = rho_window9(b, plane, ev.nbx, w, me.x, me.y, p.dc2);
             else
-                r = rho_select(b, plane, ev.nbx, w, xi, yi, p.dc2);
+                r = rho_select(b, plane, ev.nbx, w, me.x, me.y, p.dc2);
             b.rho_s[q] = r;
         }
     }
@@ -142,35 +222,37 @@ cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cu
 // nh_i: over the window of radius d_m, the (d2, j)-lexicographic minimum among
 // hits with d2 < d_m^2 and rho_j > rho_i (the minimum is order-free).  Writes
 // rho, delta^2 and nh back by hit index.
-__global__ void __launch_bounds__(512) k_nh(Buffers b, Params p) {
+__global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
+    const float4 *__restrict__ sp = b.sp;
+    const float *__restrict__ rs = b.rho_s;
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const EventDesc ev = b.events[tl.event];
         const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
-            const float xi = b.xs[q], yi = b.ys[q], ri = b.rho_s[q];
+            const float4 me = sp[q];
+            const float ri = rs[q];
             const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
-            const Window w = window_of(xi, yi, p.rwin_nh, ev);
+            const Window w = window_of(me.x, me.y, p.rwin_nh, ev);
             float best = __int_as_float(0x7f800000);  // +inf
             int bj = INT_MAX;
             for (int by = w.ly; by <= w.hy; ++by) {
                 const int64_t row = plane + (int64_t)by * ev.nbx;
                 const int e = b.cell_start[row + w.hx + 1];
                 for (int u = b.cell_start[row + w.lx]; u < e; ++u) {
-                    if (b.rho_s[u] > ri) {
-                        const float d2 = sq_dist(xi, yi, b.xs[u], b.ys[u]);
-                        if (d2 < p.dm2) {
-                            const int j = b.ids_s[u];
-                            if (d2 < best || (d2 == best && j < bj)) {
-                                best = d2;
-                                bj = j;
-                            }
+                    if (rs[u] > ri) {
+                        const float4 h = sp[u];
+                        const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                        const int j = id_of(h);
+                        if (d2 < p.dm2 && (d2 < best || (d2 == best && j < bj))) {
+                            best = d2;
+                            bj = j;
                         }
                     }
                 }
             }
-            const int g = b.ids_s[q];
+            const int g = id_of(me);
             b.rho[g] = ri;
             b.delta2[g] = best;
             b.nh[g] = bj == INT_MAX ? -1 : bj;

@@ -5,9 +5,10 @@
 // is a counting sort with a canonical result: hits are counted per cell,
 // cell offsets come from a prefix sum, hits are scattered into their cell's
 // segment, and every segment is then put in ascending hit index.  The sorted
-// copies of x, y and w make every later neighbour scan a walk over contiguous
-// memory, and the ascending order inside each cell is what lets the density
-// step sum in ascending hit index.
+// copy (x, y, w, id packed in one float4 per hit, one 16-byte load per
+// candidate) makes every later neighbour scan a walk over contiguous memory,
+// and the ascending order inside each cell is what lets the density step sum
+// in ascending hit index.
 #include "scan.cuh"
 
 namespace clue {
@@ -30,7 +31,7 @@ __global__ void __launch_bounds__(256) k_fill_count(Buffers b, Params p) {
             const int by = axis_bin(y, ev.ymin, ev.inv_s, ev.nby);
             const int local = (l * ev.nby + by) * ev.nbx + bx;
             b.key[g] = local;
-            atomicAdd(&b.count[ev.cell_off + local], 1);
+            b.rank[g] = atomicAdd(&b.count[ev.cell_off + local], 1);
             b.fcount[g] = 0;  // follower counters of the decision step
         }
     }
@@ -52,17 +53,17 @@ cudaError_t launch_scan_cells(const Buffers &b, const LaunchCfg &c, cudaStream_t
                                    (int32_t *)b.scan_partials, c.grid_cap, s, launches);
 }
 
-// --- scatter: every hit into its cell's segment (order within a cell is not
-// yet fixed; `count` is consumed as the per-cell cursor) ---------------------
+// --- scatter: every hit into its cell's segment at the rank its count
+// returned (order within a cell is not yet fixed).  The hit travels as one
+// 16-byte record (x, y, w, id): one scattered store, no atomic. --------------
 __global__ void __launch_bounds__(256) k_fill_scatter(Buffers b) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int64_t coff = b.events[tl.event].cell_off;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int g = tl.start + k;
-            const int64_t c = coff + b.key[g];
-            const int slot = b.cell_start[c] + atomicSub(&b.count[c], 1) - 1;
-            b.perm[slot] = g;
+            const int slot = b.cell_start[coff + b.key[g]] + b.rank[g];
+            b.rec[slot] = make_float4(b.x[g], b.y[g], b.w[g], __int_as_float(g));
         }
     }
 }
@@ -84,18 +85,17 @@ __global__ void __launch_bounds__(256) k_fill_canon(Buffers b) {
         const int ev_nbxy = ev.nbx * ev.nby;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int pos = tl.start + k;
-            const int g = b.perm[pos];
-            const int64_t c = coff + b.key[g];
+            const float4 r = b.rec[pos];
+            const int g = __float_as_int(r.w);
+            const int local = b.key[g];
+            const int64_t c = coff + local;
             const int a = b.cell_start[c], e = b.cell_start[c + 1];
             if (e - a <= SMALL_SEGMENT) {
                 int rank = 0;
-                for (int q = a; q < e; ++q) rank += (b.perm[q] < g);
+                for (int q = a; q < e; ++q) rank += (__float_as_int(b.rec[q].w) < g);
                 const int dst = a + rank;
-                b.ids_s[dst] = g;
-                b.xs[dst] = b.x[g];
-                b.ys[dst] = b.y[g];
-                b.ws[dst] = b.w[g];
-                b.lay_s[dst] = b.key[g] / (ev_nbxy);
+                b.sp[dst] = r;
+                b.lay_s[dst] = local / ev_nbxy;
             } else if (pos == a) {
                 const int i = atomicAdd(&b.ctrl->nbig, 1);
                 b.big[i] = (int32_t)(c);
@@ -111,9 +111,9 @@ cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t
 }
 
 // --- CTA sorter for long segments: a stable least-significant-digit radix
-// sort (8-bit digits) of the segment's hit ids, in place between `perm` and
-// `tmp` (both hold the segment at the same offsets, so no memory is shared
-// between segments).  Stability within a chunk comes from warp match masks,
+// sort (8-bit digits) of the segment's hit ids, read from the slot records
+// and then passed between `tmp` and `perm` (both hold the segment at the same
+// offsets, so no memory is shared between segments).  Stability within a chunk comes from warp match masks,
 // across chunks from processing them in order. ---------------------------------
 constexpr int BIG_THREADS = 256;
 constexpr int BIG_WARPS = BIG_THREADS / 32;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_fill_big(Buffers b) {
         // layer of the cell: the event is that of any hit in the segment
         int lay;
         {
-            const int g0 = b.perm[a];
+            const int g0 = __float_as_int(b.rec[a].w);
             int lo = 0, hi = b.nevents - 1;  // event of g0 by bisection on hit_off
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_fill_big(Buffers b) {
         // range of ids in the segment
         int vmin = 0x7fffffff, vmax = 0;
         for (int i = tid; i < h; i += BIG_THREADS) {
-            const int v = b.perm[a + i];
+            const int v = __float_as_int(b.rec[a + i].w);
             vmin = min(vmin, v);
             vmax = max(vmax, v);
         }
@@ -167,15 +167,19 @@ __global__ void __launch_bounds__(BIG_THREADS) k_fill_big(Buffers b) {
         const unsigned range = (unsigned)(vmax - vmin);
         const int bits = range ? 32 - __clz(range) : 1;
         const int passes = (bits + 7) / 8;
-        int *src = b.perm + a, *dst = b.tmp + a;
+        // pass 0 reads the records' ids (absolute); later passes ping-pong
+        // relative ids between tmp and perm
+        const float4 *rec = b.rec + a;
+        int *src = nullptr, *dst = b.tmp + a, *other = b.perm + a;
         for (int pass = 0; pass < passes; ++pass) {
             const int shift = 8 * pass;
-            const int sub = pass == 0 ? vmin : 0;  // pass 0 reads absolute ids
+            const int sub = pass == 0 ? vmin : 0;
+#define SRC(i) (pass == 0 ? __float_as_int(rec[(i)].w) : src[(i)])
             hist[tid] = 0;
             for (int w = 0; w < BIG_WARPS; ++w) wcount[w][tid] = 0;
             __syncthreads();
             for (int i = tid; i < h; i += BIG_THREADS)
-                atomicAdd(&hist[((unsigned)(src[i] - sub) >> shift) & 255], 1);
+                atomicAdd(&hist[((unsigned)(SRC(i) - sub) >> shift) & 255], 1);
             __syncthreads();
             {
                 int total;
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_fill_big(Buffers b) {
             for (int c0 = 0; c0 < h; c0 += BIG_THREADS) {
                 const int i = c0 + tid;
                 const bool valid = i < h;
-                const unsigned v = valid ? (unsigned)(src[i] - sub) : 0u;
+                const unsigned v = valid ? (unsigned)(SRC(i) - sub) : 0u;
                 const int d = valid ? (int)((v >> shift) & 255) : 256;
                 const unsigned peers = __match_any_sync(FULL_MASK, d);
                 const int lrank = __popc(peers & lanemask_lt());
@@ -206,18 +210,16 @@ __global__ void __launch_bounds__(BIG_THREADS) k_fill_big(Buffers b) {
                 base[tid] += add;
                 __syncthreads();
             }
-            int *t = src;
-            src = dst;
-            dst = t;
+#undef SRC
+            src = dst;  // this pass's output is the next pass's input
+            dst = other;
+            other = src;
         }
         // src now holds the sorted ids relative to vmin
         for (int i = tid; i < h; i += BIG_THREADS) {
             const int g = src[i] + vmin;
             const int q = a + i;
-            b.ids_s[q] = g;
-            b.xs[q] = b.x[g];
-            b.ys[q] = b.y[g];
-            b.ws[q] = b.w[g];
+            b.sp[q] = make_float4(b.x[g], b.y[g], b.w[g], __int_as_float(g));
             b.lay_s[q] = lay;
         }
         __syncthreads();
