@@ -379,6 +379,22 @@ def main():
     for k, v in kern.items():
         stages[clue.STAGE_OF.get(k, k)] = stages.get(clue.STAGE_OF.get(k, k), 0.0) + v
 
+    # ---- the same batch with the level-by-level frontier expansion ---------
+    cl_f = clue.Clusterer(device=local, extent=gen.EXTENT, max_layers=100,
+                          expand=clue.CLUE_EXPAND_FRONTIER)
+    cl_f.tuning = tuning
+    for _ in range(3):
+        cl_f.run_batch(tx, ty, tl, te, offs, PARAMS, out=(cid, seed))
+    cl_f.sync()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(cl_f.stream)
+    for _ in range(10):
+        cl_f.run_batch(tx, ty, tl, te, offs, PARAMS, out=(cid, seed))
+    f1.record(cl_f.stream)
+    f1.synchronize()
+    frontier_value = N / (f0.elapsed_time(f1) / 10 * 1e-3) / 1e6
+    cl_f.close()
+
     # ---- per-event launches (same events, one clue_run each) -------------
     cl_pe = clue.Clusterer(device=local, extent=gen.EXTENT, max_layers=100, use_graphs=False)
     cl_pe.tuning = tuning
@@ -459,6 +475,8 @@ def main():
             "config": {"workload": WORKLOAD, "global_batch": len(events) * ws,
                        "hits_per_step": hits_all, "parallelism": f"replicas x{ws}",
                        "l2": "inputs (1 GB per rank) larger than L2, no flush"},
+            "batched_frontier_expansion": {"value": frontier_value, "unit": "Mhits/s",
+                                           "kind": "same batch, CLUE_EXPAND_FRONTIER"},
             "per_event": {"value": per_event_value, "unit": "Mhits/s", "events": len(idx),
                           "hits": pe_hits, "kind": "one clue_run per event, back to back"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)),

@@ -69,15 +69,23 @@ typedef struct clue_opts {
                             multiple of 32); 0 = tuned */
     int32_t use_graphs;  /* 1 = capture a repeated call into a CUDA graph and replay it */
     void *stream;        /* cudaStream_t to queue work on; NULL = context-owned stream */
+    int32_t expand;      /* how ids reach the followers (identical results):
+                            CLUE_EXPAND_FRONTIER = follower lists walked level by
+                            level from the seeds (Algorithm 3's expansion, k-way);
+                            CLUE_EXPAND_CHASE = each follower follows its nh chain
+                            up to the first hit with a final id (n-way) */
 } clue_opts;
 
+#define CLUE_EXPAND_FRONTIER 0
+#define CLUE_EXPAND_CHASE 1
+
 /* Defaults: device 0, extent [-250, 250]^2, 128 layers, tuned bin/block,
- * graphs on, own stream. */
+ * graphs on, own stream, expansion by chasing (CLUE_EXPAND_CHASE). */
 void clue_default_opts(clue_opts *opts);
 
 /* Create a context on opts->device.  *out receives the context.
  * Errors: CLUE_ERR_ARG (null, extent not finite/increasing, max_layers < 1,
- * bin_size < 0), CLUE_ERR_CUDA. */
+ * bin_size < 0, block_size or expand out of range), CLUE_ERR_CUDA. */
 int clue_create(clue_ctx **out, const clue_opts *opts);
 
 /* Release the context and everything it owns (waits for its work first). */

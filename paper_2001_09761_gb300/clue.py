@@ -37,7 +37,10 @@ class ClueOpts(ctypes.Structure):
                 ("y_min", ctypes.c_float), ("y_max", ctypes.c_float),
                 ("max_layers", ctypes.c_int32), ("bin_size", ctypes.c_float),
                 ("block_size", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("expand", ctypes.c_int32)]
+
+
+CLUE_EXPAND_FRONTIER, CLUE_EXPAND_CHASE = 0, 1
 
 
 class ClueError(RuntimeError):
@@ -195,7 +198,7 @@ STAGE_OF = {"fill_count": "grid_fill", "scan_cells": "grid_fill", "fill_scatter"
             "fill_canon": "grid_fill", "fill_big": "grid_fill", "rho": "rho",
             "nh_delta": "nh_delta", "decide": "decide_followers",
             "scan_hits": "decide_followers", "link": "decide_followers",
-            "expand_level": "expand", "complete": "expand"}
+            "expand_level": "expand", "complete": "expand", "chase": "expand"}
 
 
 def clue_last_launch_count(ctx) -> int:
@@ -247,7 +250,7 @@ class Clusterer:
 
     def __init__(self, device: int = 0, extent=(-250.0, 250.0, -250.0, 250.0),
                  max_layers: int = 128, bin_size: float = 0.0, block_size: int = 0,
-                 use_graphs: bool = True):
+                 use_graphs: bool = True, expand: int = CLUE_EXPAND_CHASE):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -260,6 +263,7 @@ class Clusterer:
         o.block_size = int(block_size)
         o.use_graphs = 1 if use_graphs else 0
         o.stream = self.stream.cuda_stream
+        o.expand = int(expand)
         self.max_layers = max_layers
         self.ctx = clue_create(o)
         self._last_n = 0

@@ -141,6 +141,7 @@ Params make_params(const clue_ctx *ctx, float dc, float rhoc, float delta_c, flo
     p.rwin_rho = dc * grow;
     p.rwin_nh = dm * grow;
     p.L = ctx->opts.max_layers;
+    p.chase = ctx->opts.expand == CLUE_EXPAND_CHASE;
     return p;
 }
 
@@ -216,14 +217,10 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     b.sp = (float4 *)take(n * 16);
     b.lay_s = (int32_t *)take(n * 4);
     // one 16-byte-per-hit region: the grid fill's slot records, then (after
-    // the fill) rho in sorted order, rho, delta^2 and nh by hit
+    // the fill) the per-hit records rho, delta^2, nh of the nh step
     b.rec = (float4 *)take(n * 16);
-    if (!dry) {
-        b.rho_s = (float *)b.rec;
-        b.rho = b.rho_s + n;
-        b.delta2 = b.rho + n;
-        b.nh = (int32_t *)(b.delta2 + n);
-    }
+    b.hr = b.rec;
+    b.rho_s = (float *)take(n * 4);
     b.flags = (uint8_t *)take(n);
     b.fcount = (int32_t *)take(n * 4);
     b.hs = (unsigned long long *)take((n + 1) * 8);
@@ -360,15 +357,21 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(rec("decide"));
     CK(launch_scan_hits(b, cfg, s, &nl));
     CK(rec("scan_hits"));
-    CK(launch_link(b, cfg, s));
+    CK(launch_link(b, p, cfg, s));
     CK(rec("link"));
-    for (int level = 0; level < EXPAND_LEVELS; ++level) {
-        CK(launch_expand_level(b, cfg, level, s));
-        CK(rec("expand_level"));
+    if (p.chase) {
+        CK(launch_chase(b, cfg, s));
+        CK(rec("chase"));
+        nl += 5;  // rho, nh, decide, link, chase
+    } else {
+        for (int level = 0; level < EXPAND_LEVELS; ++level) {
+            CK(launch_expand_level(b, cfg, level, s));
+            CK(rec("expand_level"));
+        }
+        CK(launch_complete(b, cfg, s));
+        CK(rec("complete"));
+        nl += 5 + EXPAND_LEVELS;  // rho, nh, decide, link, complete, levels
     }
-    CK(launch_complete(b, cfg, s));
-    CK(rec("complete"));
-    nl += 5 + EXPAND_LEVELS;
     *launches = nl;
     return CLUE_OK;
 }
@@ -519,6 +522,7 @@ void clue_default_opts(clue_opts *o) {
     o->block_size = 0;
     o->use_graphs = 1;
     o->stream = nullptr;
+    o->expand = CLUE_EXPAND_CHASE;
 }
 
 int clue_create(clue_ctx **out, const clue_opts *opts) {
@@ -528,7 +532,8 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
     if (!std::isfinite(o.x_min) || !std::isfinite(o.x_max) || !std::isfinite(o.y_min) ||
         !std::isfinite(o.y_max) || !(o.x_max > o.x_min) || !(o.y_max > o.y_min) ||
         o.max_layers < 1 || !(o.bin_size >= 0.0f) || !std::isfinite(o.bin_size) ||
-        o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
+        o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0 ||
+        (o.expand != CLUE_EXPAND_FRONTIER && o.expand != CLUE_EXPAND_CHASE))
         return CLUE_ERR_ARG;
     clue_ctx *ctx = new (std::nothrow) clue_ctx();
     if (!ctx) return CLUE_ERR_OOM;

@@ -64,6 +64,7 @@ struct Params {
     float rwin_rho;  // d_c * (1 + 2^-12): window half-width before the |v| margin
     float rwin_nh;   // d_m * (1 + 2^-12)
     int32_t L;       // layers per event (grid planes)
+    int32_t chase;   // 1: expansion by chasing nh chains (no follower lists)
 };
 
 // Device pointers of one run, carved from the scratch arena.
@@ -86,7 +87,7 @@ struct Buffers {
     int32_t *count;      // [C] hits per cell (zeroed per run)
     int32_t *cell_start; // [C + 1]
     float4 *rec;         // [N] hits grouped by cell, unordered within a cell:
-                         //     x, y, w, id (int bits); aliases rho_s..nh
+                         //     x, y, w, id (int bits); aliases hr
     int32_t *perm;       // [N] scratch of the CTA sorter
     int32_t *tmp;        // [N] scratch for the CTA sorter
     int32_t *big;        // [N / SMALL_SEGMENT + 1] cells queued for the CTA sorter
@@ -94,9 +95,7 @@ struct Buffers {
     int32_t *lay_s;      // [N] layer in sorted order
     // density
     float *rho_s;        // [N] rho in sorted order
-    float *rho;          // [N] rho by hit
-    float *delta2;       // [N] squared separation by hit
-    int32_t *nh;         // [N] nearest-higher (batch index) or -1
+    float4 *hr;          // [N] by hit: rho, delta^2, nh (int bits: batch index or -1)
     // decision / expansion
     uint8_t *flags;      // [N]
     int32_t *fcount;     // [N] followers per hit (zeroed in the fill step)
@@ -129,7 +128,8 @@ cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cu
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_decide(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
-cudaError_t launch_link(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_chase(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);  // all levels
 cudaError_t launch_expand_level(const Buffers &b, const LaunchCfg &c, int level, cudaStream_t s);
 cudaError_t launch_complete(const Buffers &b, const LaunchCfg &c, cudaStream_t s);

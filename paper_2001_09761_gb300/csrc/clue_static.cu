@@ -39,7 +39,7 @@ constexpr size_t STATIC_BYTES =
     al(NB * 4) /*key*/ + al(NB * 4) /*rank*/ + al(CB * 4) /*count*/ + al((CB + 1) * 4) /*cell_start*/ +
     al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ + al((NB / SMALL_SEGMENT + 1) * 4) /*big*/ +
     al(NB * 16) /*sp*/ + al(NB * 4) /*lay_s*/ +
-    al(NB * 16) /*rec = rho_s, rho, delta2, nh*/ +
+    al(NB * 16) /*rec = hr*/ + al(NB * 4) /*rho_s*/ +
     al(NB) /*flags*/ + al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
     al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/;
 
@@ -139,10 +139,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.sp = (float4 *)take(NB * 16);
     b.lay_s = (int32_t *)take(NB * 4);
     b.rec = (float4 *)take(NB * 16);
-    b.rho_s = (float *)b.rec;
-    b.rho = b.rho_s + NB;
-    b.delta2 = b.rho + NB;
-    b.nh = (int32_t *)(b.delta2 + NB);
+    b.hr = b.rec;
+    b.rho_s = (float *)take(NB * 4);
     b.flags = (uint8_t *)take(NB);
     b.fcount = (int32_t *)take(NB * 4);
     b.hs = (unsigned long long *)take((NB + 1) * 8);
@@ -197,6 +195,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     prm.rwin_rho = dc * (1.0f + 0x1p-12f);
     prm.rwin_nh = dm * (1.0f + 0x1p-12f);
     prm.L = max_layers;
+    prm.chase = 0;
     LaunchCfg cfg;
     cfg.block_fill = 256;
     cfg.block_density = 256;
@@ -226,7 +225,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     SCK(launch_nh(b, prm, cfg, s));
     SCK(launch_decide(b, prm, cfg, s));
     SCK(launch_scan_hits(b, cfg, s, &nl));
-    SCK(launch_link(b, cfg, s));
+    SCK(launch_link(b, prm, cfg, s));
     SCK(launch_expand(b, cfg, s));
     SCK(launch_complete(b, cfg, s));
     Ctrl h{};

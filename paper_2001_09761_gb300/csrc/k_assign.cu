@@ -18,13 +18,14 @@ __global__ void __launch_bounds__(256) k_decide(Buffers b, Params p) {
         const Tile tl = b.tiles[t];
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int g = tl.start + k;
-            const float r = b.rho[g], d2 = b.delta2[g];
-            const int j = b.nh[g];
+            const float4 h = b.hr[g];
+            const float r = h.x, d2 = h.y;
+            const int j = __float_as_int(h.z);
             const bool seed = (r > p.rhoc) && (d2 > p.dcs2);
             const bool outl = (r < p.rhoc) && (d2 > p.dos2);
             const bool fol = !seed && !outl && j >= 0;
             b.flags[g] = (seed ? F_SEED : 0) | (outl ? F_OUTLIER : 0) | (fol ? F_FOLLOWER : 0);
-            if (fol) b.frank[g] = atomicAdd(&b.fcount[j], 1);
+            if (fol && !p.chase) b.frank[g] = atomicAdd(&b.fcount[j], 1);
         }
     }
 }
@@ -56,7 +57,7 @@ cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t 
 // of their nearest-higher at the rank the decision step's count returned
 // (order inside a list is irrelevant: each follower has exactly one parent);
 // everything else is noise for now.
-__global__ void __launch_bounds__(256) k_link(Buffers b) {
+__global__ void __launch_bounds__(256) k_link(Buffers b, Params p) {
     __shared__ int ws[32];
     __shared__ int s_base;
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
@@ -77,8 +78,10 @@ __global__ void __launch_bounds__(256) k_link(Buffers b) {
                 } else {
                     b.is_seed[g] = 0;
                     if (f & F_FOLLOWER) {
-                        const int j = b.nh[g];
-                        b.fol[(int)(unsigned)b.hs[j] + b.frank[g]] = g;
+                        if (!p.chase) {
+                            const int j = __float_as_int(b.hr[g].z);
+                            b.fol[(int)(unsigned)b.hs[j] + b.frank[g]] = g;
+                        }
                         b.cid[g] = PENDING;
                     } else {
                         b.cid[g] = -1;
@@ -97,9 +100,45 @@ __global__ void __launch_bounds__(256) k_link(Buffers b) {
     }
 }
 
-cudaError_t launch_link(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
+cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
     const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
-    k_link<<<grid > 0 ? grid : 1, c.block_fill, 0, s>>>(b);
+    k_link<<<grid > 0 ? grid : 1, c.block_fill, 0, s>>>(b, p);
+    return cudaGetLastError();
+}
+
+// Expansion by chasing (CLUE_EXPAND_CHASE): every follower still pending
+// follows its nh chain up to the first hit with a final id -- a seed's id, an
+// id another thread already resolved (a benign race: a pending entry reads as
+// pending or as its final value), or -1 at an outlier or a hit with no
+// nearest-higher -- and takes it: the closed form "a follower inherits the id
+// of its nearest-higher".  The chain is finite because rho rises strictly
+// along it; the walk is still bounded by N steps.
+__global__ void __launch_bounds__(256) k_chase(Buffers b) {
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+        const Tile tl = b.tiles[t];
+        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+            const int g = tl.start + k;
+            if (b.cid[g] != PENDING) continue;
+            int v = __float_as_int(b.hr[g].z);
+            int cv = b.cid[v];
+            int64_t steps = 0;
+            while (cv == PENDING && steps < b.N) {
+                v = __float_as_int(b.hr[v].z);
+                cv = b.cid[v];
+                ++steps;
+            }
+            if (cv == PENDING) {
+                atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
+                cv = -1;
+            }
+            b.cid[g] = cv;
+        }
+    }
+}
+
+cudaError_t launch_chase(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
+    const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
+    k_chase<<<grid > 0 ? grid : 1, 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -200,11 +239,11 @@ __global__ void __launch_bounds__(256) k_complete(Buffers b) {
                 b.cid[g] = -1;
                 continue;
             }
-            int v = b.nh[g];
+            int v = __float_as_int(b.hr[g].z);
             int cv = b.cid[v];
             int64_t steps = 0;
             while (cv == PENDING && steps < b.N) {
-                v = b.nh[v];
+                v = __float_as_int(b.hr[v].z);
                 cv = b.cid[v];
                 ++steps;
             }
@@ -229,10 +268,11 @@ __global__ void __launch_bounds__(256) k_export(Buffers b, float *rho, float *de
         const int64_t hoff = b.events[tl.event].hit_off;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int g = tl.start + k;
-            if (rho) rho[g] = b.rho[g];
-            if (delta) delta[g] = sqrtf(b.delta2[g]);
+            const float4 h = b.hr[g];
+            if (rho) rho[g] = h.x;
+            if (delta) delta[g] = sqrtf(h.y);
             if (nh) {
-                const int j = b.nh[g];
+                const int j = __float_as_int(h.z);
                 nh[g] = j < 0 ? -1 : (int32_t)(j - hoff);
             }
         }

@@ -190,7 +190,7 @@ __device__ __forceinline__ float rho_window4(const Buffers &b, int64_t plane, in
     return r;
 }
 
-__global__ void __launch_bounds__(256) k_rho(Buffers b, Params p) {
+__global__ void __launch_bounds__(256, 1) k_rho(Buffers b, Params p) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const EventDesc ev = b.events[tl.event];
@@ -221,7 +221,8 @@ cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cu
 
 // nh_i: over the window of radius d_m, the (d2, j)-lexicographic minimum among
 // hits with d2 < d_m^2 and rho_j > rho_i (the minimum is order-free).  Writes
-// rho, delta^2 and nh back by hit index.
+// rho, delta^2 and nh back by hit index as one 16-byte record (one scattered
+// store per hit; separate 4-byte stores cost three).
 __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
     const float4 *__restrict__ sp = b.sp;
     const float *__restrict__ rs = b.rho_s;
@@ -240,22 +241,17 @@ __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
             for (int by = w.ly; by <= w.hy; ++by) {
                 const int64_t row = plane + (int64_t)by * ev.nbx;
                 const int e = b.cell_start[row + w.hx + 1];
-                for (int u = b.cell_start[row + w.lx]; u < e; ++u) {
-                    if (rs[u] > ri) {
-                        const float4 h = sp[u];
-                        const float d2 = sq_dist(me.x, me.y, h.x, h.y);
-                        const int j = id_of(h);
-                        if (d2 < p.dm2 && (d2 < best || (d2 == best && j < bj))) {
-                            best = d2;
-                            bj = j;
-                        }
-                    }
+                for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
+                    const float ru = rs[u];
+                    const float4 h = sp[u];
+                    const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                    const int j = id_of(h);
+                    const bool take = (ru > ri) & (d2 < p.dm2) & ((d2 < best) | ((d2 == best) & (j < bj)));
+                    best = take ? d2 : best;
+                    bj = take ? j : bj;
                 }
             }
-            const int g = id_of(me);
-            b.rho[g] = ri;
-            b.delta2[g] = best;
-            b.nh[g] = bj == INT_MAX ? -1 : bj;
+            b.hr[id_of(me)] = make_float4(ri, best, __int_as_float(bj == INT_MAX ? -1 : bj), 0.0f);
         }
     }
 }

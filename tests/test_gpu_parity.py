@@ -92,10 +92,11 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("expand", [0, 1], ids=["frontier", "chase"])
 @pytest.mark.parametrize("kind,n,L,params,seed,ext", CASES)
-def test_parity_vs_oracle(clue_mod, kind, n, L, params, seed, ext):
+def test_parity_vs_oracle(clue_mod, kind, n, L, params, seed, ext, expand):
     ev = gen.make_event(n, L, seed, kind, extent=ext)
-    cl = _cl(clue_mod, ext, L)
+    cl = _cl(clue_mod, ext, L, expand=expand)
     g = _gpu_all(cl, ev, params)
     ref = oracle.run_event(ev, params, L, extent=ext)
     assert_parity(g, ref)
@@ -197,7 +198,8 @@ def test_dense_cells_use_the_cta_sorter(clue_mod):
     assert_parity(_gpu_all(cl, ev, p), oracle.run_event(ev, p, 1, extent=ext))
 
 
-def test_wide_tree_one_node_with_many_followers(clue_mod):
+@pytest.mark.parametrize("expand", [0, 1], ids=["frontier", "chase"])
+def test_wide_tree_one_node_with_many_followers(clue_mod, expand):
     """2000 hits on a circle of radius 3 around one heavy hit.  They are
     farther apart than d_c, so each has rho = its own weight 1 (equal, so none
     is higher than another), and the centre (rho 1000) is every one's
@@ -211,10 +213,24 @@ def test_wide_tree_one_node_with_many_followers(clue_mod):
     ev = Ev(x, y, np.zeros(k + 2, np.int32), w)
     p = (0.005, 0.5, 4.0, 4.0)
     ext = (-100.0, 100.0, -100.0, 100.0)
-    cl = _cl(clue_mod, ext, 1)
+    cl = _cl(clue_mod, ext, 1, expand=expand)
     ref = oracle.run_event(ev, p, 1, extent=ext)
     assert (ref["nh"][1:k + 1] == 0).all() and (ref["cluster_id"][1:k + 1] == 0).all()
     assert_parity(_gpu_all(cl, ev, p), ref)
+
+
+@pytest.mark.parametrize("expand", [0, 1], ids=["frontier", "chase"])
+def test_batch_expand_modes_agree(clue_mod, expand):
+    evs = [gen.make_event(n, 100, 800 + i, k) for i, (n, k) in
+           enumerate([(30000, "blobs"), (50000, "irregular"), (3, "blobs"), (0, "blobs")])]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = _cl(clue_mod, gen.EXTENT, 100, expand=expand)
+    cid, seed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_IRREGULAR)
+    cl.sync()
+    cid = cid.cpu().numpy()
+    for i, ev in enumerate(evs):
+        ref = oracle.run_event(ev, gen.PARAMS_IRREGULAR, 100)
+        assert np.array_equal(cid[offs[i]:offs[i + 1]], ref["cluster_id"])
 
 
 def test_long_chain(clue_mod):
@@ -225,6 +241,9 @@ def test_long_chain(clue_mod):
     ev = Ev(x - 500.0, np.zeros(n), np.zeros(n, np.int32), w)
     p = (1.5, 1.0, 2.0, 3.0)
     ext = (-600.0, 600.0, -10.0, 10.0)
+    for expand in (0, 1):
+        cl = _cl(clue_mod, ext, 1, expand=expand)
+        assert_parity(_gpu_all(cl, ev, p), oracle.run_event(ev, p, 1, extent=ext))
     cl = _cl(clue_mod, ext, 1)
     ref = oracle.run_event(ev, p, 1, extent=ext)
     assert_parity(_gpu_all(cl, ev, p), ref)
@@ -265,12 +284,13 @@ def test_autotune_keeps_results(clue_mod):
 
 def test_stage_times_and_launch_count(clue_mod):
     ev = gen.make_event(100_000, 100, 3, "blobs")
-    cl = _cl(clue_mod, gen.EXTENT, 100)
-    cl.set_profiling(True)
-    cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_BLOBS)
-    st = cl.stage_times()
-    assert list(st) == ["grid_fill", "rho", "nh_delta", "decide_followers", "expand"]
-    assert all(v >= 0 for v in st.values())
-    kt = cl.kernel_times()
-    assert {"fill_count", "rho", "nh_delta", "expand_level", "complete"} <= set(kt)
-    assert cl.launch_count() == 15 + 12  # 12 expansion levels
+    for expand, last in ((0, {"expand_level", "complete"}), (1, {"chase"})):
+        cl = _cl(clue_mod, gen.EXTENT, 100, expand=expand)
+        cl.set_profiling(True)
+        cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_BLOBS)
+        st = cl.stage_times()
+        assert list(st) == ["grid_fill", "rho", "nh_delta", "decide_followers", "expand"]
+        assert all(v >= 0 for v in st.values())
+        kt = cl.kernel_times()
+        assert {"fill_count", "rho", "nh_delta"} | last <= set(kt)
+        assert cl.launch_count() == (15 + 12 if expand == 0 else 15)
