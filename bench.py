@@ -164,13 +164,14 @@ def run_reference(args):
 # read once and every result written once (no re-reads, no scratch beyond
 # the stage's own outputs).
 ALG_BYTES = {
-    "fill_count": 16 + 4 + 4 + 4,      # x, y, w, layer in; key, follower counter, cell count
-    "fill_scatter": 4 + 4 + 4,         # key, cell offset in; slot out
-    "fill_canon": 4 + 4 + 8 + 12 + 20,  # slot, key, cell range, x/y/w in; sorted copies out
-    "rho": 16 + 4,                     # x, y, w, layer in; rho out
-    "nh_delta": 16 + 12,               # x, y, rho, layer in; rho, delta^2, nh out
-    "decide": 12 + 1 + 4,              # rho, delta^2, nh in; flags, follower count out
-    "link": 1 + 8 + 4 + 4 + 1 + 4,     # flags, prefix, nh in; id, seed flag, list slot out
+    "fill_count": 16 + 4 + 4 + 4,      # x, y, w, layer in; cell, rank, cell count out
+    "fill_scatter": 4 + 4 + 4 + 12 + 16,  # cell, rank, cell start, x/y/w in; record out
+    "fill_canon": 16 + 4 + 8 + 16 + 4,  # record, cell, cell range in; sorted hit, layer out
+    "rho": 16 + 4 + 4,                 # x, y, w, id, layer in; rho out
+    "nh_delta": 16 + 4 + 4 + 12,       # x, y, id, rho, layer in; rho, delta^2, nh out
+    "decide": 12 + 1,                  # rho, delta^2, nh in; flags out
+    "link": 1 + 8 + 4 + 4 + 1,         # flags, prefix, nh in; id, seed flag out
+    "chase": 4 + 4 + 4,                # id, nh in; id out
     "expand_level": 8 + 4 + 4 + 4,     # list range, parent id, follower in; id out
     "complete": 4 + 4,                 # id in, id out
 }
@@ -248,6 +249,12 @@ def extra_configs(torch, clue, tuning, dev, args):
     res["scaling_sweep_median_mhits_per_s"] = sweep
     irr = gen.irregular_event(0)
     res["irregular_5M"] = single(irr, 50, gen.PARAMS_IRREGULAR, 5, "c4")
+    # Sec. 4.2's own workload shape and parameters (bin 5 cm), 100 x 10k hits;
+    # the paper's V100 numbers for it are context only (other hardware)
+    pap = single(gen.make_event(1_000_000, 100, 0, "paper"), 100, gen.PARAMS_PAPER, 10, "f3")
+    pap["paper_v100_context"] = {"kernels_ms": 2.37, "total_with_memcpy_ms": 6.63,
+                                 "cpu_1thread_ms": 705.49, "source": "Table 2"}
+    res["paper_parameters_1M"] = pap
     return res
 
 

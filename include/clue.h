@@ -14,8 +14,9 @@
  *   - distances are compared squared in fp32: dx = x_j - x_i, dy = y_j - y_i,
  *     d2 = dx*dx + dy*dy, each operation rounded to nearest, no fused
  *     multiply-add; thresholds are squared once in fp32;
- *   - chi is flat: rho_i is the fp32 sum, from +0 in ascending hit index j, of
- *     w_j over all hits j of i's layer with d2 < d_c^2 (j = i included);
+ *   - chi is flat unless clue_opts.chi says otherwise: rho_i is the fp32 sum,
+ *     from +0 in ascending hit index j, of w_j (or fl(chi(d_ij) w_j)) over all
+ *     hits j of i's layer with d2 < d_c^2 (j = i included);
  *   - nh_i is the hit j of i's layer with rho_j > rho_i and d2 < d_m^2,
  *     d_m = max(delta_c, delta_o), of smallest d2, the smaller index on a tie;
  *     -1 (and delta = +inf) when there is none;
@@ -74,7 +75,17 @@ typedef struct clue_opts {
                             level from the seeds (Algorithm 3's expansion, k-way);
                             CLUE_EXPAND_CHASE = each follower follows its nh chain
                             up to the first hit with a final id (n-way) */
+    int32_t chi;         /* density kernel chi(d) of Eq. 3: CLUE_CHI_FLAT (1, the
+                            default), CLUE_CHI_GAUSSIAN exp(-d^2 / (2 s^2)),
+                            CLUE_CHI_EXPONENTIAL exp(-d / s); the term added is
+                            fl(chi(d) * w), with exp computed by a fixed fp32
+                            sequence (Cody-Waite reduction, degree-7 Taylor) */
+    float chi_param;     /* s > 0 for the Gaussian and exponential kernels */
 } clue_opts;
+
+#define CLUE_CHI_FLAT 0
+#define CLUE_CHI_GAUSSIAN 1
+#define CLUE_CHI_EXPONENTIAL 2
 
 #define CLUE_EXPAND_FRONTIER 0
 #define CLUE_EXPAND_CHASE 1
@@ -85,7 +96,8 @@ void clue_default_opts(clue_opts *opts);
 
 /* Create a context on opts->device.  *out receives the context.
  * Errors: CLUE_ERR_ARG (null, extent not finite/increasing, max_layers < 1,
- * bin_size < 0, block_size or expand out of range), CLUE_ERR_CUDA. */
+ * bin_size < 0, block_size, expand or chi out of range, chi_param not > 0
+ * for a non-flat chi), CLUE_ERR_CUDA. */
 int clue_create(clue_ctx **out, const clue_opts *opts);
 
 /* Release the context and everything it owns (waits for its work first). */

@@ -40,13 +40,14 @@ def _load():
     if _lib is None:
         build()
         lib = ctypes.CDLL(str(_LIB))
-        f = lib.oracle_clue
+        f = lib.oracle_clue_chi
         P = ctypes.c_void_p
-        f.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int32,
-                      ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                      ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                      P, P, P, P, P, P, P, P]
+        F = ctypes.c_float
+        f.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int32, F, F, F, F, F, F, F, F,
+                      ctypes.c_int32, F, P, P, P, P, P, P, P, P]
         f.restype = ctypes.c_int
+        lib.oracle_chi_exp.argtypes = [F]
+        lib.oracle_chi_exp.restype = F
         _lib = lib
     return _lib
 
@@ -55,10 +56,18 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
 
 
-def run(x, y, layer, energy, params, n_layers, extent=(-250.0, 250.0, -250.0, 250.0)):
+def chi_exp(a: float) -> float:
+    """The oracle's fp32 exp(a) for a <= 0 (used by the Gaussian and
+    exponential kernels)."""
+    return float(_load().oracle_chi_exp(float(a)))
+
+
+def run(x, y, layer, energy, params, n_layers, extent=(-250.0, 250.0, -250.0, 250.0),
+        chi=0, chi_param=0.0):
     """Cluster one event; returns a dict of numpy arrays (see clue_oracle.c).
 
-    params = (d_c, rho_c, delta_c, delta_o).  Raises ValueError on the
+    params = (d_c, rho_c, delta_c, delta_o); chi = 0 flat, 1 Gaussian, 2
+    exponential kernel with width chi_param.  Raises ValueError on the
     oracle's error codes.
     """
     lib = _load()
@@ -73,9 +82,9 @@ def run(x, y, layer, energy, params, n_layers, extent=(-250.0, 250.0, -250.0, 25
                cluster_id=np.empty(n, np.int32))
     k = ctypes.c_int64(0)
     dc, rhoc, delta_c, delta_o = params
-    rc = lib.oracle_clue(n, _ptr(x), _ptr(y), _ptr(layer), _ptr(energy), int(n_layers),
+    rc = lib.oracle_clue_chi(n, _ptr(x), _ptr(y), _ptr(layer), _ptr(energy), int(n_layers),
                          *[float(v) for v in extent], float(dc), float(rhoc),
-                         float(delta_c), float(delta_o),
+                         float(delta_c), float(delta_o), int(chi), float(chi_param),
                          _ptr(out["rho"]), _ptr(out["delta"]), _ptr(out["delta2"]),
                          _ptr(out["nh"]), _ptr(out["is_seed"]), _ptr(out["is_outlier"]),
                          _ptr(out["cluster_id"]), ctypes.byref(k))
@@ -85,8 +94,9 @@ def run(x, y, layer, energy, params, n_layers, extent=(-250.0, 250.0, -250.0, 25
     return out
 
 
-def run_event(ev, params, n_layers, extent=(-250.0, 250.0, -250.0, 250.0)):
-    return run(ev.x, ev.y, ev.layer, ev.energy, params, n_layers, extent)
+def run_event(ev, params, n_layers, extent=(-250.0, 250.0, -250.0, 250.0), chi=0,
+              chi_param=0.0):
+    return run(ev.x, ev.y, ev.layer, ev.energy, params, n_layers, extent, chi, chi_param)
 
 
 def run_batch(x, y, layer, energy, offsets, params, n_layers,

@@ -11,7 +11,8 @@
  * What it computes, step by step in the paper's order:
  *   1. a fixed square grid per layer (Sec. 2.1, Eqs. 1-2), each bin listing
  *      its hits in ascending hit index;
- *   2. local density rho (Eq. 3, Algorithm 1) with the flat kernel chi = 1;
+ *   2. local density rho (Eq. 3, Algorithm 1) with the flat kernel chi = 1,
+ *      or (oracle_clue_chi) the Gaussian or exponential kernel Eq. 3 names;
  *   3. nearest-higher nh and separation delta (Eq. 4, Algorithm 2);
  *   4. seed / outlier decision and follower registration (Sec. 2.2, Eq. 5,
  *      first half of Algorithm 3);
@@ -20,7 +21,10 @@
  *
  * Readings where the paper is silent or ambiguous (each is also listed in the
  * design notes of the repository):
- *   R1  chi is flat: every j with d_ij < d_c adds w_j, j = i included.
+ *   R1  chi is flat: every j with d_ij < d_c adds w_j, j = i included.  The
+ *       Gaussian and exponential kernels add fl(chi(d_ij) * w_j), chi computed
+ *       by oracle_chi_exp below; the paper gives them no parameters, so their
+ *       width s is an input.
  *   R2  d_ij is Euclidean in (x, y) on the same layer only, compared squared in
  *       fp32: dx = x_j - x_i, dy = y_j - y_i, d2 = dx*dx + dy*dy, every
  *       operation rounded to nearest with no fused multiply-add (this file is
@@ -85,6 +89,45 @@ static double window_half(double d, double v)
     return d * (1.0 + 1e-6) + fabs(v) * 1e-9;
 }
 
+/* exp(a) for a <= 0 in fp32, written from the mathematics: Cody and Waite's
+ * reduction (W. J. Cody, W. Waite, "Software Manual for the Elementary
+ * Functions", 1980) a = k ln2 + r with ln2 split into a short constant L1
+ * (exact products k L1) and its remainder L2, |r| <= ln2 / 2, then
+ * exp(r) by its Taylor series to degree 7 in Horner form and exp(a) =
+ * 2^k exp(r).  Every operation is one fp32 rounding in a fixed order.
+ * Arguments below -87 give 0 (results there would be subnormal). */
+float oracle_chi_exp(float a)
+{
+    if (!(a > -87.0f))
+        return 0.0f;
+    const float kf = floorf(a * 1.44269504f + 0.5f);     /* round(a / ln2) */
+    const float r = (a - kf * 0.693359375f) + kf * 2.12194440e-4f;
+    float p = 1.98412698e-4f;                            /* 1/7! */
+    p = p * r + 1.38888889e-3f;                          /* 1/6! */
+    p = p * r + 8.33333333e-3f;                          /* 1/5! */
+    p = p * r + 4.16666667e-2f;                          /* 1/4! */
+    p = p * r + 1.66666667e-1f;                          /* 1/3! */
+    p = p * r + 0.5f;                                    /* 1/2! */
+    p = p * r + 1.0f;
+    p = p * r + 1.0f;
+    const int32_t bits = ((int32_t)kf + 127) << 23;      /* 2^k, -125 <= k <= 0 */
+    float scale;
+    memcpy(&scale, &bits, sizeof(scale));
+    return p * scale;
+}
+
+/* The convolution kernel chi(d_ij) of Eq. 3 for squared distance d2:
+ * kind 0 flat (1), 1 Gaussian exp(-d2 / (2 s^2)), 2 exponential exp(-d / s),
+ * with s = param > 0; inv is fl(1 / fl(2 s s)) or fl(1 / s). */
+static float chi_value(int32_t kind, float inv, float d2)
+{
+    if (kind == 1)
+        return oracle_chi_exp(-(d2 * inv));
+    if (kind == 2)
+        return oracle_chi_exp(-(sqrtf(d2) * inv));
+    return 1.0f;
+}
+
 static int cmp_int64(const void *a, const void *b)
 {
     int64_t p = *(const int64_t *)a, q = *(const int64_t *)b;
@@ -103,13 +146,18 @@ static int param_ok(float d)
  *   is_seed (0/1), is_outlier (0/1), cluster_id (0..k-1 or -1).
  * Any output pointer may be NULL.  Returns ORACLE_OK or a negative code.
  */
-int oracle_clue(int64_t n, const float *x, const float *y, const int32_t *layer,
-                const float *w, int32_t n_layers, float x_min, float x_max,
-                float y_min, float y_max, float dc, float rhoc, float delta_c,
-                float delta_o, float *rho_out, float *delta_out, float *delta2_out,
-                int32_t *nh_out, uint8_t *is_seed_out, uint8_t *is_outlier_out,
-                int32_t *cluster_id_out, int64_t *n_seeds_out)
+int oracle_clue_chi(int64_t n, const float *x, const float *y, const int32_t *layer,
+                    const float *w, int32_t n_layers, float x_min, float x_max,
+                    float y_min, float y_max, float dc, float rhoc, float delta_c,
+                    float delta_o, int32_t chi_kind, float chi_param, float *rho_out,
+                    float *delta_out, float *delta2_out, int32_t *nh_out,
+                    uint8_t *is_seed_out, uint8_t *is_outlier_out,
+                    int32_t *cluster_id_out, int64_t *n_seeds_out)
 {
+    if (chi_kind < 0 || chi_kind > 2 || (chi_kind != 0 && !(chi_param > 0.0f && isfinite(chi_param))))
+        return ORACLE_ERR_ARG;
+    const float chi_inv = chi_kind == 1 ? 1.0f / (2.0f * (chi_param * chi_param))
+                        : chi_kind == 2 ? 1.0f / chi_param : 1.0f;
     if (n < 0 || n_layers <= 0 || !(dc > 0.0f) || !param_ok(dc) || !param_ok(delta_c) ||
         !param_ok(delta_o) || !isfinite(rhoc) || !isfinite(x_min) || !isfinite(x_max) ||
         !isfinite(y_min) || !isfinite(y_max) || !(x_max > x_min) || !(y_max > y_min))
@@ -190,8 +238,15 @@ int oracle_clue(int64_t n, const float *x, const float *y, const int32_t *layer,
                         buf[m++] = j;
         qsort(buf, (size_t)m, sizeof(int64_t), cmp_int64);
         float r = 0.0f;
-        for (int64_t k = 0; k < m; ++k)
-            r += w[buf[k]];
+        for (int64_t k = 0; k < m; ++k) {
+            const int64_t j = buf[k];
+            if (chi_kind == 0) {
+                r += w[j];
+            } else {
+                const float t = chi_value(chi_kind, chi_inv, sq_dist(x[i], y[i], x[j], y[j])) * w[j];
+                r += t;
+            }
+        }
         rho[i] = r;
     }
 
@@ -264,4 +319,17 @@ int oracle_clue(int64_t n, const float *x, const float *y, const int32_t *layer,
     free(head); free(next); free(buf); free(rho); free(d2v); free(nh); free(cid);
     free(fol_head); free(fol_next); free(stack); free(seed); free(outl);
     return ORACLE_OK;
+}
+
+/* Flat-kernel CLUE (chi = 1, as Algorithm 1). */
+int oracle_clue(int64_t n, const float *x, const float *y, const int32_t *layer,
+                const float *w, int32_t n_layers, float x_min, float x_max,
+                float y_min, float y_max, float dc, float rhoc, float delta_c,
+                float delta_o, float *rho_out, float *delta_out, float *delta2_out,
+                int32_t *nh_out, uint8_t *is_seed_out, uint8_t *is_outlier_out,
+                int32_t *cluster_id_out, int64_t *n_seeds_out)
+{
+    return oracle_clue_chi(n, x, y, layer, w, n_layers, x_min, x_max, y_min, y_max, dc, rhoc,
+                           delta_c, delta_o, 0, 0.0f, rho_out, delta_out, delta2_out, nh_out,
+                           is_seed_out, is_outlier_out, cluster_id_out, n_seeds_out);
 }

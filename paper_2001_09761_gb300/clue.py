@@ -37,10 +37,12 @@ class ClueOpts(ctypes.Structure):
                 ("y_min", ctypes.c_float), ("y_max", ctypes.c_float),
                 ("max_layers", ctypes.c_int32), ("bin_size", ctypes.c_float),
                 ("block_size", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("expand", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("expand", ctypes.c_int32),
+                ("chi", ctypes.c_int32), ("chi_param", ctypes.c_float)]
 
 
 CLUE_EXPAND_FRONTIER, CLUE_EXPAND_CHASE = 0, 1
+CLUE_CHI_FLAT, CLUE_CHI_GAUSSIAN, CLUE_CHI_EXPONENTIAL = 0, 1, 2
 
 
 class ClueError(RuntimeError):
@@ -250,7 +252,8 @@ class Clusterer:
 
     def __init__(self, device: int = 0, extent=(-250.0, 250.0, -250.0, 250.0),
                  max_layers: int = 128, bin_size: float = 0.0, block_size: int = 0,
-                 use_graphs: bool = True, expand: int = CLUE_EXPAND_CHASE):
+                 use_graphs: bool = True, expand: int = CLUE_EXPAND_CHASE,
+                 chi: int = CLUE_CHI_FLAT, chi_param: float = 0.0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -264,6 +267,8 @@ class Clusterer:
         o.use_graphs = 1 if use_graphs else 0
         o.stream = self.stream.cuda_stream
         o.expand = int(expand)
+        o.chi = int(chi)
+        o.chi_param = float(chi_param)
         self.max_layers = max_layers
         self.ctx = clue_create(o)
         self._last_n = 0

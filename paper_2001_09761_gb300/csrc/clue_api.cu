@@ -142,6 +142,10 @@ Params make_params(const clue_ctx *ctx, float dc, float rhoc, float delta_c, flo
     p.rwin_nh = dm * grow;
     p.L = ctx->opts.max_layers;
     p.chase = ctx->opts.expand == CLUE_EXPAND_CHASE;
+    p.chi = ctx->opts.chi;
+    const float sp = ctx->opts.chi_param;
+    p.chi_inv = p.chi == CLUE_CHI_GAUSSIAN ? 1.0f / (2.0f * (sp * sp))
+              : p.chi == CLUE_CHI_EXPONENTIAL ? 1.0f / sp : 1.0f;
     return p;
 }
 
@@ -220,7 +224,7 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     // the fill) the per-hit records rho, delta^2, nh of the nh step
     b.rec = (float4 *)take(n * 16);
     b.hr = b.rec;
-    b.rho_s = (float *)take(n * 4);
+    b.spr = (float4 *)take(n * 16);
     b.flags = (uint8_t *)take(n);
     b.fcount = (int32_t *)take(n * 4);
     b.hs = (unsigned long long *)take((n + 1) * 8);
@@ -523,6 +527,8 @@ void clue_default_opts(clue_opts *o) {
     o->use_graphs = 1;
     o->stream = nullptr;
     o->expand = CLUE_EXPAND_CHASE;
+    o->chi = CLUE_CHI_FLAT;
+    o->chi_param = 0.0f;
 }
 
 int clue_create(clue_ctx **out, const clue_opts *opts) {
@@ -533,7 +539,9 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
         !std::isfinite(o.y_max) || !(o.x_max > o.x_min) || !(o.y_max > o.y_min) ||
         o.max_layers < 1 || !(o.bin_size >= 0.0f) || !std::isfinite(o.bin_size) ||
         o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0 ||
-        (o.expand != CLUE_EXPAND_FRONTIER && o.expand != CLUE_EXPAND_CHASE))
+        (o.expand != CLUE_EXPAND_FRONTIER && o.expand != CLUE_EXPAND_CHASE) ||
+        o.chi < CLUE_CHI_FLAT || o.chi > CLUE_CHI_EXPONENTIAL ||
+        (o.chi != CLUE_CHI_FLAT && !(o.chi_param > 0.0f && std::isfinite(o.chi_param))))
         return CLUE_ERR_ARG;
     clue_ctx *ctx = new (std::nothrow) clue_ctx();
     if (!ctx) return CLUE_ERR_OOM;

@@ -65,6 +65,8 @@ struct Params {
     float rwin_nh;   // d_m * (1 + 2^-12)
     int32_t L;       // layers per event (grid planes)
     int32_t chase;   // 1: expansion by chasing nh chains (no follower lists)
+    int32_t chi;     // density kernel: 0 flat, 1 Gaussian, 2 exponential
+    float chi_inv;   // 1 / (2 s^2) (Gaussian) or 1 / s (exponential)
 };
 
 // Device pointers of one run, carved from the scratch arena.
@@ -94,7 +96,7 @@ struct Buffers {
     float4 *sp;          // [N] hits sorted by (cell, id): x, y, w, id (int bits)
     int32_t *lay_s;      // [N] layer in sorted order
     // density
-    float *rho_s;        // [N] rho in sorted order
+    float4 *spr;         // [N] sorted order: x, y, rho, id (written by the rho step)
     float4 *hr;          // [N] by hit: rho, delta^2, nh (int bits: batch index or -1)
     // decision / expansion
     uint8_t *flags;      // [N]

@@ -39,7 +39,7 @@ constexpr size_t STATIC_BYTES =
     al(NB * 4) /*key*/ + al(NB * 4) /*rank*/ + al(CB * 4) /*count*/ + al((CB + 1) * 4) /*cell_start*/ +
     al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ + al((NB / SMALL_SEGMENT + 1) * 4) /*big*/ +
     al(NB * 16) /*sp*/ + al(NB * 4) /*lay_s*/ +
-    al(NB * 16) /*rec = hr*/ + al(NB * 4) /*rho_s*/ +
+    al(NB * 16) /*rec = hr*/ + al(NB * 16) /*spr*/ +
     al(NB) /*flags*/ + al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
     al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/;
 
@@ -140,7 +140,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.lay_s = (int32_t *)take(NB * 4);
     b.rec = (float4 *)take(NB * 16);
     b.hr = b.rec;
-    b.rho_s = (float *)take(NB * 4);
+    b.spr = (float4 *)take(NB * 16);
     b.flags = (uint8_t *)take(NB);
     b.fcount = (int32_t *)take(NB * 4);
     b.hs = (unsigned long long *)take((NB + 1) * 8);
@@ -196,6 +196,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     prm.rwin_nh = dm * (1.0f + 0x1p-12f);
     prm.L = max_layers;
     prm.chase = 0;
+    prm.chi = 0;
+    prm.chi_inv = 1.0f;
     LaunchCfg cfg;
     cfg.block_fill = 256;
     cfg.block_density = 256;

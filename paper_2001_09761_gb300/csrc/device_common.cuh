@@ -38,6 +38,39 @@ __device__ __forceinline__ float win_half(float dr, float v) {
     return __fadd_rn(dr, __fmul_rn(fabsf(v), 0x1p-20f));
 }
 
+// exp(a) for a <= 0 in fp32, from the mathematics: Cody and Waite's
+// reduction (W. J. Cody, W. Waite, "Software Manual for the Elementary
+// Functions", 1980) a = k ln2 + r with ln2 = L1 + L2 (L1 short, so k L1 is
+// exact), |r| <= ln2 / 2, exp(r) by its Taylor series to degree 7 (Horner),
+// exp(a) = 2^k exp(r).  Each step is one round-to-nearest fp32 operation in a
+// fixed order, so the result is reproducible bit for bit on any IEEE machine.
+// a below -87 gives 0 (the result there would be subnormal).
+__device__ __forceinline__ float chi_exp(float a) {
+    if (!(a > -87.0f)) return 0.0f;
+    const float kf = floorf(__fadd_rn(__fmul_rn(a, 1.44269504f), 0.5f));
+    const float r = __fadd_rn(__fsub_rn(a, __fmul_rn(kf, 0.693359375f)),
+                              __fmul_rn(kf, 2.12194440e-4f));
+    float p = 1.98412698e-4f;
+    p = __fadd_rn(__fmul_rn(p, r), 1.38888889e-3f);
+    p = __fadd_rn(__fmul_rn(p, r), 8.33333333e-3f);
+    p = __fadd_rn(__fmul_rn(p, r), 4.16666667e-2f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.66666667e-1f);
+    p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    return __fmul_rn(p, __int_as_float(((int)kf + 127) << 23));
+}
+
+// The kernel chi(d) of Eq. 3 on squared distance d2: flat (1), Gaussian
+// exp(-d2 inv) with inv = 1 / (2 s^2), exponential exp(-sqrt(d2) inv) with
+// inv = 1 / s.
+template <int CHI>
+__device__ __forceinline__ float chi_of(float d2, float inv) {
+    if (CHI == 1) return chi_exp(-__fmul_rn(d2, inv));
+    if (CHI == 2) return chi_exp(-__fmul_rn(__fsqrt_rn(d2), inv));
+    return 1.0f;
+}
+
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -7,7 +7,9 @@
 // the sorted array, so a window row is one contiguous run.  Each sorted hit is
 // one float4 (x, y, w, id), so a candidate costs one 16-byte load.
 //
-// rho is summed in fp32 in ascending hit index j over N_dc(i) (the order is
+// rho is summed in fp32 in ascending hit index j over N_dc(i) of chi(d_ij) w_j
+// (flat chi = 1 unless the context asks for the Gaussian or exponential kernel
+// that Eq. 3 names; chi is computed by chi_exp, bit-reproducible) (the order is
 // part of the result's definition, independent of the bin size): every cell
 // lists its hits in ascending index, and the kernel merges the lists of the
 // window's non-empty cells, adding w_j for each j that passes the distance
@@ -36,18 +38,22 @@ __device__ __forceinline__ Window window_of(float xi, float yi, float dr, const 
 
 __device__ __forceinline__ int id_of(const float4 &h) { return __float_as_int(h.w); }
 
+// r + chi(d) w for a candidate within d_c (flat: r + w exactly).
+template <int CHI = 0>
 __device__ __forceinline__ float add_if_near(float r, float xi, float yi, const float4 &h,
-                                             float dc2) {
-    return sq_dist(xi, yi, h.x, h.y) < dc2 ? __fadd_rn(r, h.z) : r;
+                                             float dc2, float inv = 1.0f) {
+    const float d2 = sq_dist(xi, yi, h.x, h.y);
+    if (CHI == 0) return d2 < dc2 ? __fadd_rn(r, h.z) : r;
+    return d2 < dc2 ? __fadd_rn(r, __fmul_rn(chi_of<CHI>(d2, inv), h.z)) : r;
 }
 
 // Merge of up to K sorted cell lists given as [p[k], e[k]) (k < nk).  With
 // CACHE the head hit of every list stays in registers (one load per
 // candidate); without it only the head ids do (fewer registers, two loads).
-template <int K, bool CACHE>
+template <int K, bool CACHE, int CHI>
 __device__ __forceinline__ float merge_k(const float4 *__restrict__ sp, int (&p)[K],
                                          const int (&e)[K], int nk, float xi, float yi,
-                                         float dc2) {
+                                         float dc2, float inv) {
     float4 h[CACHE ? K : 1];
     int head[K];
 #pragma unroll
@@ -71,7 +77,7 @@ __device__ __forceinline__ float merge_k(const float4 *__restrict__ sp, int (&p)
         for (int k = 0; k < K; ++k)
             if (am == k) {
                 const int q = p[k]++;
-                r = add_if_near(r, xi, yi, CACHE ? h[k] : sp[q], dc2);
+                r = add_if_near<CHI>(r, xi, yi, CACHE ? h[k] : sp[q], dc2, inv);
                 const bool live = q + 1 < e[k];
                 if (CACHE) {
                     h[k] = live ? sp[q + 1] : h[k];
@@ -85,8 +91,9 @@ __device__ __forceinline__ float merge_k(const float4 *__restrict__ sp, int (&p)
 }
 
 // Windows of at most 3 x 3 cells (a bin size between d_c and 2 d_c).
+template <int CHI>
 __device__ __forceinline__ float rho_window9(const Buffers &b, int64_t plane, int nbx, const Window &w, float xi,
-                             float yi, float dc2) {
+                             float yi, float dc2, float inv) {
     int p[9], e[9];
     int nk = 0;
 #pragma unroll
@@ -111,14 +118,15 @@ __device__ __forceinline__ float rho_window9(const Buffers &b, int64_t plane, in
             }
         nk += ne;
     }
-    return merge_k<9, false>(b.sp, p, e, nk, xi, yi, dc2);
+    return merge_k<9, false, CHI>(b.sp, p, e, nk, xi, yi, dc2, inv);
 }
 
 // Any window size: repeatedly take the smallest id above the last one taken.
 // Quadratic in the window population; used only when the window spans more
 // than 3 x 3 bins (a bin size near d_c plus rounding at a bin edge).
+template <int CHI>
 __device__ __forceinline__ float rho_select(const Buffers &b, int64_t plane, int nbx, const Window &w, float xi,
-                            float yi, float dc2) {
+                            float yi, float dc2, float inv) {
     float r = 0.0f;
     int last = -1;
     while (true) {
@@ -139,7 +147,7 @@ __device__ __forceinline__ float rho_select(const Buffers &b, int64_t plane, int
                 }
             }
         if (bq < 0) break;
-        r = add_if_near(r, xi, yi, b.sp[bq], dc2);
+        r = add_if_near<CHI>(r, xi, yi, b.sp[bq], dc2, inv);
         last = best;
     }
     return r;
@@ -149,8 +157,10 @@ __device__ __forceinline__ float rho_select(const Buffers &b, int64_t plane, int
 // whose window has fewer cells just has empty cursors), so lanes of a warp
 // never take different code paths; a cursor keeps only its head id in a
 // register and the chosen candidate is loaded once.
+template <int CHI>
 __device__ __forceinline__ float rho_window4(const Buffers &b, int64_t plane, int nbx,
-                                             const Window &w, float xi, float yi, float dc2) {
+                                             const Window &w, float xi, float yi, float dc2,
+                                             float inv) {
     const float4 *__restrict__ sp = b.sp;
     const int4 *__restrict__ spi = reinterpret_cast<const int4 *>(b.sp);  // id = .w
     int p0, p1, p2, p3, e0, e1, e2, e3;
@@ -180,7 +190,7 @@ __device__ __forceinline__ float rho_window4(const Buffers &b, int64_t plane, in
         else if (m == h1) { q = p1++; e = e1; }
         else if (m == h2) { q = p2++; e = e2; }
         else { q = p3++; e = e3; }
-        r = add_if_near(r, xi, yi, sp[q], dc2);
+        r = add_if_near<CHI>(r, xi, yi, sp[q], dc2, inv);
         const int nx = q + 1 < e ? spi[q + 1].w : INT_MAX;
         if (m == h0) h0 = nx;
         else if (m == h1) h1 = nx;
@@ -190,6 +200,7 @@ __device__ __forceinline__ float rho_window4(const Buffers &b, int64_t plane, in
     return r;
 }
 
+template <int CHI>
 __global__ void __launch_bounds__(256, 1) k_rho(Buffers b, Params p) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
@@ -203,19 +214,25 @@ __global__ void __launch_bounds__(256, 1) k_rho(Buffers b, Params p) {
             const int nx = w.hx - w.lx + 1, ny = w.hy - w.ly + 1;
             float r;
             if (nx <= 2 && ny <= 2)
-                r = rho_window4(b, plane, ev.nbx, w, me.x, me.y, p.dc2);
+                r = rho_window4<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv);
             else if (nx <= 3 && ny <= 3)
-                r = rho_window9(b, plane, ev.nbx, w, me.x, me.y, p.dc2);
+                r = rho_window9<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv);
             else
-                r = rho_select(b, plane, ev.nbx, w, me.x, me.y, p.dc2);
-            b.rho_s[q] = r;
+                r = rho_select<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv);
+            b.spr[q] = make_float4(me.x, me.y, r, me.w);  // x, y, rho, id for the nh step
         }
     }
 }
 
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
     const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
-    k_rho<<<grid > 0 ? grid : 1, c.block_density, 0, s>>>(b, p);
+    const int g = grid > 0 ? grid : 1;
+    if (p.chi == 1)
+        k_rho<1><<<g, c.block_density, 0, s>>>(b, p);
+    else if (p.chi == 2)
+        k_rho<2><<<g, c.block_density, 0, s>>>(b, p);
+    else
+        k_rho<0><<<g, c.block_density, 0, s>>>(b, p);
     return cudaGetLastError();
 }
 
@@ -224,8 +241,7 @@ cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cu
 // rho, delta^2 and nh back by hit index as one 16-byte record (one scattered
 // store per hit; separate 4-byte stores cost three).
 __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
-    const float4 *__restrict__ sp = b.sp;
-    const float *__restrict__ rs = b.rho_s;
+    const float4 *__restrict__ sp = b.spr;  // x, y, rho, id
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const EventDesc ev = b.events[tl.event];
@@ -233,7 +249,7 @@ __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
             const float4 me = sp[q];
-            const float ri = rs[q];
+            const float ri = me.z;
             const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
             const Window w = window_of(me.x, me.y, p.rwin_nh, ev);
             float best = __int_as_float(0x7f800000);  // +inf
@@ -242,8 +258,8 @@ __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
                 const int64_t row = plane + (int64_t)by * ev.nbx;
                 const int e = b.cell_start[row + w.hx + 1];
                 for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
-                    const float ru = rs[u];
                     const float4 h = sp[u];
+                    const float ru = h.z;
                     const float d2 = sq_dist(me.x, me.y, h.x, h.y);
                     const int j = id_of(h);
                     const bool take = (ru > ri) & (d2 < p.dm2) & ((d2 < best) | ((d2 == best) & (j < bj)));

@@ -294,3 +294,42 @@ def test_stage_times_and_launch_count(clue_mod):
         kt = cl.kernel_times()
         assert {"fill_count", "rho", "nh_delta"} | last <= set(kt)
         assert cl.launch_count() == (15 + 12 if expand == 0 else 15)
+
+
+def test_paper_parameter_workload(clue_mod):
+    """Sec. 4.2's workload shape (unit weights, sigma 3 cm blobs, 5% noise,
+    d_c = 3, rho_c = 8, delta_c = delta_o = 5, bin 5 cm), 100 layers x 2k hits."""
+    ev = gen.make_event(200_000, 100, 11, "paper")
+    cl = _cl(clue_mod, gen.EXTENT, 100, bin_size=5.0)
+    assert_parity(_gpu_all(cl, ev, gen.PARAMS_PAPER), oracle.run_event(ev, gen.PARAMS_PAPER, 100))
+
+
+def test_noise_shrinks_as_delta_o_grows_on_gpu(clue_mod):
+    """Fig. 4: with delta_c fixed and at least every delta_o, a larger delta_o
+    demotes fewer outliers, so the noise can only shrink; each run is also
+    bit-exact with the oracle."""
+    ext = (-80.0, 80.0, -80.0, 80.0)
+    ev = gen.make_event(8000, 1, 21, "blobs", extent=ext)
+    cl = _cl(clue_mod, ext, 1)
+    prev = None
+    for do in (0.5, 1.0, 2.0, 4.0):
+        p = (2.0, 2.0, 4.0, do)
+        g = _gpu_all(cl, ev, p)
+        assert_parity(g, oracle.run_event(ev, p, 1, extent=ext))
+        noise = int((g["cluster_id"] < 0).sum())
+        if prev is not None:
+            assert noise <= prev
+        prev = noise
+
+
+@pytest.mark.parametrize("chi,s", [(1, 1.5), (2, 0.8)], ids=["gaussian", "exponential"])
+def test_chi_kernels_parity(clue_mod, chi, s):
+    """Eq. 3's Gaussian and exponential kernels: rho (and everything after it)
+    bit-exact with the oracle, both computing chi with the same fp32 exp."""
+    for kind, n, L, params, seed, ext in [("blobs", 30000, 10, gen.PARAMS_BLOBS, 2, gen.EXTENT),
+                                          ("irregular", 20000, 2, gen.PARAMS_IRREGULAR, 3,
+                                           (-60.0, 60.0, -60.0, 60.0))]:
+        ev = gen.make_event(n, L, seed, kind, extent=ext)
+        cl = _cl(clue_mod, ext, L, chi=chi, chi_param=s)
+        ref = oracle.run_event(ev, params, L, extent=ext, chi=chi, chi_param=s)
+        assert_parity(_gpu_all(cl, ev, params), ref)

@@ -328,3 +328,46 @@ def test_generators_are_seeded_and_shaped():
     assert sizes.size == 256 and sizes.min() >= 10_000 and sizes.max() <= 1_000_000
     irr = gen.make_event(10_000, 2, 0, "irregular")
     assert irr.n == 10_000
+
+
+def test_chi_exp_within_two_ulp_of_exp(oracle_mod):
+    """The oracle's fp32 exp used by the Gaussian and exponential kernels of
+    Eq. 3, against float64 exp: at most 2 ULP of the fp32 result on a dense
+    grid of [-86.9, 0], exactly 1 at 0, and 0 below -87."""
+    a = np.concatenate([np.linspace(-86.9, 0.0, 40001), -np.logspace(-12, 0, 2001)]).astype(np.float32)
+    mine = np.array([oracle_mod.chi_exp(v) for v in a], np.float64)
+    ref = np.exp(a.astype(np.float64))
+    ulp = np.spacing(ref.astype(np.float32)).astype(np.float64)
+    assert np.max(np.abs(mine - ref) / ulp) <= 2.0
+    assert oracle_mod.chi_exp(0.0) == 1.0 and oracle_mod.chi_exp(-0.0) == 1.0
+    assert oracle_mod.chi_exp(-87.5) == 0.0 and oracle_mod.chi_exp(-1e30) == 0.0
+
+
+@pytest.mark.parametrize("chi,s", [(1, 1.0), (1, 2.5), (2, 0.7), (2, 3.0)])
+def test_chi_rho_within_bound_of_exact(oracle_mod, chi, s):
+    """rho with the Gaussian (1) or exponential (2) kernel of Eq. 3: against
+    the exact float64 sum of chi(d_ij) w_j over the same neighbours, within the
+    recursive-summation bound plus the per-term error of chi (2 ULP of exp,
+    the fp32 argument and the product rounding): |err| <= 24 u sum|t| +
+    (m-1) u sum|t|."""
+    ext = (-15.0, 15.0, -15.0, 15.0)
+    ev = gen.make_event(700, 1, 4, "irregular", extent=ext)
+    dc = 2.0
+    o = oracle_mod.run_event(ev, (dc, 3.0, 2.0, 4.0), 1, extent=ext, chi=chi, chi_param=s)
+    x, y, w = ev.x, ev.y, ev.energy
+    dx = x[None, :] - x[:, None]
+    dy = y[None, :] - y[:, None]
+    d2 = dx * dx + dy * dy
+    near = d2 < np.float32(dc) * np.float32(dc)
+    dd = np.hypot(x[None, :].astype(np.float64) - x[:, None], y[None, :].astype(np.float64) - y[:, None])
+    chi_true = np.exp(-dd * dd / (2 * s * s)) if chi == 1 else np.exp(-dd / s)
+    t = np.where(near, chi_true * w[None, :].astype(np.float64), 0.0)
+    m = near.sum(1)
+    exact = t.sum(1)
+    u = 2.0 ** -24
+    bound = (24 * u + (m - 1) * u) * np.abs(t).sum(1) + 1e-37
+    assert np.all(np.abs(o["rho"].astype(np.float64) - exact) <= bound)
+    # and the flat kernel is the special case chi = 1
+    flat = oracle_mod.run_event(ev, (dc, 3.0, 2.0, 4.0), 1, extent=ext)
+    big = oracle_mod.run_event(ev, (dc, 3.0, 2.0, 4.0), 1, extent=ext, chi=0, chi_param=0.0)
+    assert np.array_equal(flat["rho"], big["rho"])
