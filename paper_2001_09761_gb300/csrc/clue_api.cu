@@ -79,6 +79,8 @@ struct clue_ctx {
     int num_sms = 0;
     cudaStream_t own = nullptr;
     cudaStream_t stream = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr;  // copy streams of the host-pointer path
+    cudaEvent_t chunk_in[8] = {}, chunk_done[8] = {};
     char *arena = nullptr;
     size_t arena_cap = 0;
     void *dtables = nullptr;
@@ -599,6 +601,16 @@ void clue_destroy(clue_ctx *ctx) {
     }
     for (auto &ev : ctx->pev)
         if (ev) cudaEventDestroy(ev);
+    if (ctx->h2d) {
+        cudaStreamSynchronize(ctx->h2d);
+        cudaStreamSynchronize(ctx->d2h);
+        cudaStreamDestroy(ctx->h2d);
+        cudaStreamDestroy(ctx->d2h);
+        for (int i = 0; i < 8; ++i) {
+            cudaEventDestroy(ctx->chunk_in[i]);
+            cudaEventDestroy(ctx->chunk_done[i]);
+        }
+    }
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
 }
@@ -687,27 +699,57 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
     if (!ctx || n_events < 0 || (n_events > 0 && !offsets)) return CLUE_ERR_ARG;
     if (n_events == 0) return CLUE_OK;
     const int64_t N = offsets[n_events];
-    if (N < 0 || N > MAX_HITS) return CLUE_ERR_ARG;
+    if (N < 0 || N > MAX_HITS || offsets[0] != 0) return CLUE_ERR_ARG;
+    for (int32_t e = 0; e < n_events; ++e)
+        if (offsets[e + 1] < offsets[e]) return CLUE_ERR_ARG;
     if (N == 0) return check_params(dc, rhoc, delta_c, delta_o);
     if (!x || !y || !layer || !energy || !cluster_id || !is_seed) return CLUE_ERR_ARG;
-    CK(cudaSetDevice(ctx->device));
-    const size_t n = (size_t)N;
-    HostIO io;
-    int rc0 = ensure_hio(ctx, N, io);
-    if (rc0) return rc0;
-    float *dx = io.x, *dy = io.y, *de = io.e;
-    int32_t *dl = io.l, *dc_out = io.cid;
-    uint8_t *ds = io.seed;
-    cudaStream_t s = ctx->stream;
-    CK(cudaMemcpyAsync(dx, x, n * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(dy, y, n * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(dl, layer, n * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(de, energy, n * 4, cudaMemcpyHostToDevice, s));
-    int rc = run_batch(ctx, dx, dy, dl, de, offsets, n_events, dc, rhoc, delta_c, delta_o, dc_out,
-                       ds, true);
+    int rc = check_params(dc, rhoc, delta_c, delta_o);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(cluster_id, dc_out, n * 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(is_seed, ds, n, cudaMemcpyDeviceToHost, s));
+    CK(cudaSetDevice(ctx->device));
+    HostIO io;
+    rc = ensure_hio(ctx, N, io);
+    if (rc) return rc;
+    if (!ctx->h2d) {
+        CK(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking));
+        for (int i = 0; i < 8; ++i) {
+            CK(cudaEventCreateWithFlags(&ctx->chunk_in[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ctx->chunk_done[i], cudaEventDisableTiming));
+        }
+    }
+    // Split the batch at event boundaries into up to 8 chunks of about equal
+    // hits (at least 4M hits each), so that the copy of chunk c+1 in and the
+    // copy of chunk c-1 out overlap the clustering of chunk c.
+    const int64_t target = std::max<int64_t>(N / 8, 4 << 20);
+    std::vector<int32_t> cuts{0};
+    for (int32_t e = 1; e < n_events && (int)cuts.size() < 8; ++e)
+        if (offsets[e] - offsets[cuts.back()] >= target) cuts.push_back(e);
+    cuts.push_back(n_events);
+    // the previous call's output copies must be done before the buffers are reused
+    CK(cudaStreamSynchronize(ctx->d2h));
+    std::vector<int64_t> sub;
+    for (size_t c = 0; c + 1 < cuts.size(); ++c) {
+        const int32_t e0 = cuts[c], e1 = cuts[c + 1];
+        const int64_t a = offsets[e0], nb = offsets[e1] - a;
+        const size_t n4 = (size_t)nb * 4;
+        CK(cudaMemcpyAsync(io.x + a, x + a, n4, cudaMemcpyHostToDevice, ctx->h2d));
+        CK(cudaMemcpyAsync(io.y + a, y + a, n4, cudaMemcpyHostToDevice, ctx->h2d));
+        CK(cudaMemcpyAsync(io.l + a, layer + a, n4, cudaMemcpyHostToDevice, ctx->h2d));
+        CK(cudaMemcpyAsync(io.e + a, energy + a, n4, cudaMemcpyHostToDevice, ctx->h2d));
+        CK(cudaEventRecord(ctx->chunk_in[c], ctx->h2d));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->chunk_in[c], 0));
+        sub.assign(offsets + e0, offsets + e1 + 1);
+        for (auto &v : sub) v -= a;
+        rc = run_batch(ctx, io.x + a, io.y + a, io.l + a, io.e + a, sub.data(), e1 - e0, dc, rhoc,
+                       delta_c, delta_o, io.cid + a, io.seed + a, true);
+        if (rc) return rc;
+        CK(cudaEventRecord(ctx->chunk_done[c], ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->d2h, ctx->chunk_done[c], 0));
+        CK(cudaMemcpyAsync(cluster_id + a, io.cid + a, n4, cudaMemcpyDeviceToHost, ctx->d2h));
+        CK(cudaMemcpyAsync(is_seed + a, io.seed + a, (size_t)nb, cudaMemcpyDeviceToHost, ctx->d2h));
+    }
+    CK(cudaStreamSynchronize(ctx->d2h));
     return clue_sync(ctx);
 }
 

@@ -165,6 +165,24 @@ def test_host_pointer_path(clue_mod):
             assert np.array_equal(seed[offs[i]:offs[i + 1]], ref["is_seed"])
 
 
+def test_host_pointer_path_pipelined_chunks(clue_mod):
+    """A 10M-hit batch is split into several chunks whose copies overlap the
+    clustering; the results equal the device-pointer path's."""
+    evs = [gen.make_event(n, 100, 1700 + i, "blobs")
+           for i, n in enumerate([900_000, 1_500_000, 2_000_000, 700_000, 2_500_000, 30_000,
+                                  1_200_000, 1_300_000])]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    dcid, dseed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    cl.sync()
+    dcid, dseed = dcid.cpu().numpy(), dseed.cpu().numpy()
+    for _ in range(3):  # the second call replays captured graphs
+        hcid, hseed = cl.run_batch_host(x, y, l, e, offs, gen.PARAMS_BLOBS)
+        assert np.array_equal(hcid, dcid) and np.array_equal(hseed, dseed)
+    ref = oracle.run_event(evs[5], gen.PARAMS_BLOBS, 100)
+    assert np.array_equal(hcid[offs[5]:offs[6]], ref["cluster_id"])
+
+
 def test_edge_cases(clue_mod):
     cl = _cl(clue_mod, (-10.0, 10.0, -10.0, 10.0), 4)
     p = (1.0, 0.5, 1.0, 2.0)
