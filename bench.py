@@ -287,6 +287,20 @@ def served(torch, clue, tuning, dev, peak_mhits, args):
     return out
 
 
+def profile_case():
+    """The small case the ncu captures use: 10 scaling events (100 layers x
+    10k hits, seeds 0-9, 10M hits, inputs 160 MB > L2) clustered twice as one
+    batch with the default tuning and no graph; prints nothing else."""
+    from paper_2001_09761_gb300 import clue
+    evs = [gen.scaling_event(10000, s) for s in range(10)]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = clue.Clusterer(extent=gen.EXTENT, max_layers=100, use_graphs=False)
+    for _ in range(2):
+        cl.run_batch(x, y, l, e, offs, PARAMS)
+    cl.sync()
+    print("profile case ok", int(offs[-1]))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,7 +319,11 @@ def main():
     ap.add_argument("--pool", type=int, default=32)
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--loads", type=float, nargs="*", default=[0.1, 0.5, 0.9])
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the ncu case only: 10 events x 100 layers x 10k hits, twice")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case()
     if args.warmup < 3:
         args.warmup = 3
     if args.full:
