@@ -113,25 +113,44 @@ cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, c
 // nearest-higher -- and takes it: the closed form "a follower inherits the id
 // of its nearest-higher".  The chain is finite because rho rises strictly
 // along it; the walk is still bounded by N steps.
-__global__ void __launch_bounds__(256) k_chase(Buffers b) {
+__global__ void __launch_bounds__(256, 2) k_chase(Buffers b) {
+    constexpr int U = 4;  // hits in flight per thread: their walks overlap
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
-        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-            const int g = tl.start + k;
-            if (b.cid[g] != PENDING) continue;
-            int v = __float_as_int(b.hr[g].z);
-            int cv = b.cid[v];
+        for (int k0 = threadIdx.x; k0 < tl.len; k0 += U * blockDim.x) {
+            int v[U], cv[U];
+            bool act[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = k0 + u * (int)blockDim.x;
+                act[u] = k < tl.len && b.cid[tl.start + k] == PENDING;
+                v[u] = act[u] ? __float_as_int(b.hr[tl.start + k].z) : 0;
+                cv[u] = PENDING;
+            }
             int64_t steps = 0;
-            while (cv == PENDING && steps < b.N) {
-                v = __float_as_int(b.hr[v].z);
-                cv = b.cid[v];
+            bool any = true;
+            while (any && steps <= b.N) {
+                any = false;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (act[u] && cv[u] == PENDING) cv[u] = b.cid[v[u]];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (act[u] && cv[u] == PENDING) {
+                        v[u] = __float_as_int(b.hr[v[u]].z);
+                        any = true;
+                    }
                 ++steps;
             }
-            if (cv == PENDING) {
-                atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
-                cv = -1;
-            }
-            b.cid[g] = cv;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (act[u]) {
+                    if (cv[u] == PENDING) {
+                        atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
+                        cv[u] = -1;
+                    }
+                    b.cid[tl.start + k0 + u * (int)blockDim.x] = cv[u];
+                }
         }
     }
 }
