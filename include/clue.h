@@ -81,6 +81,9 @@ typedef struct clue_opts {
                             fl(chi(d) * w), with exp computed by a fixed fp32
                             sequence (Cody-Waite reduction, degree-7 Taylor) */
     float chi_param;     /* s > 0 for the Gaussian and exponential kernels */
+    int64_t max_scratch_bytes; /* 0 = no limit; otherwise a run whose scratch
+                                  would exceed it fails with CLUE_ERR_OOM before
+                                  any allocation (memory budgets, tests) */
 } clue_opts;
 
 #define CLUE_CHI_FLAT 0

@@ -38,7 +38,8 @@ class ClueOpts(ctypes.Structure):
                 ("max_layers", ctypes.c_int32), ("bin_size", ctypes.c_float),
                 ("block_size", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("expand", ctypes.c_int32),
-                ("chi", ctypes.c_int32), ("chi_param", ctypes.c_float)]
+                ("chi", ctypes.c_int32), ("chi_param", ctypes.c_float),
+                ("max_scratch_bytes", ctypes.c_int64)]
 
 
 CLUE_EXPAND_FRONTIER, CLUE_EXPAND_CHASE = 0, 1
@@ -253,7 +254,8 @@ class Clusterer:
     def __init__(self, device: int = 0, extent=(-250.0, 250.0, -250.0, 250.0),
                  max_layers: int = 128, bin_size: float = 0.0, block_size: int = 0,
                  use_graphs: bool = True, expand: int = CLUE_EXPAND_CHASE,
-                 chi: int = CLUE_CHI_FLAT, chi_param: float = 0.0):
+                 chi: int = CLUE_CHI_FLAT, chi_param: float = 0.0,
+                 max_scratch_bytes: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -269,6 +271,7 @@ class Clusterer:
         o.expand = int(expand)
         o.chi = int(chi)
         o.chi_param = float(chi_param)
+        o.max_scratch_bytes = int(max_scratch_bytes)
         self.max_layers = max_layers
         self.ctx = clue_create(o)
         self._last_n = 0

@@ -252,6 +252,10 @@ void drop_graphs(clue_ctx *ctx) {
 
 int ensure_arena(clue_ctx *ctx, size_t need) {
     if (need <= ctx->arena_cap) return CLUE_OK;
+    if (ctx->opts.max_scratch_bytes > 0 && (int64_t)need > ctx->opts.max_scratch_bytes) {
+        ctx->msg = "scratch limit (max_scratch_bytes) exceeded";
+        return CLUE_ERR_OOM;
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     drop_graphs(ctx);
     if (ctx->arena) cudaFree(ctx->arena);
@@ -531,6 +535,7 @@ void clue_default_opts(clue_opts *o) {
     o->expand = CLUE_EXPAND_CHASE;
     o->chi = CLUE_CHI_FLAT;
     o->chi_param = 0.0f;
+    o->max_scratch_bytes = 0;
 }
 
 int clue_create(clue_ctx **out, const clue_opts *opts) {
@@ -542,7 +547,7 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
         o.max_layers < 1 || !(o.bin_size >= 0.0f) || !std::isfinite(o.bin_size) ||
         o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0 ||
         (o.expand != CLUE_EXPAND_FRONTIER && o.expand != CLUE_EXPAND_CHASE) ||
-        o.chi < CLUE_CHI_FLAT || o.chi > CLUE_CHI_EXPONENTIAL ||
+        o.chi < CLUE_CHI_FLAT || o.chi > CLUE_CHI_EXPONENTIAL || o.max_scratch_bytes < 0 ||
         (o.chi != CLUE_CHI_FLAT && !(o.chi_param > 0.0f && std::isfinite(o.chi_param))))
         return CLUE_ERR_ARG;
     clue_ctx *ctx = new (std::nothrow) clue_ctx();

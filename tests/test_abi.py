@@ -38,7 +38,7 @@ def test_host_only_calls(lib):
     assert clue.clue_version().startswith("clue-gb300")
     o = clue.clue_default_opts()
     assert (o.x_min, o.x_max, o.max_layers, o.use_graphs) == (-250.0, 250.0, 128, 1)
-    assert o.expand == clue.CLUE_EXPAND_CHASE
+    assert o.expand == clue.CLUE_EXPAND_CHASE and o.chi == 0 and o.max_scratch_bytes == 0
     # null arguments are rejected before any CUDA call
     assert lib.clue_run(None, None, None, None, None, 10, 2.0, 2.0, 2.0, 4.0, None, None) == \
         clue.CLUE_ERR_ARG

@@ -351,3 +351,35 @@ def test_chi_kernels_parity(clue_mod, chi, s):
         cl = _cl(clue_mod, ext, L, chi=chi, chi_param=s)
         ref = oracle.run_event(ev, params, L, extent=ext, chi=chi, chi_param=s)
         assert_parity(_gpu_all(cl, ev, params), ref)
+
+
+def test_scratch_limit_fails_cleanly_then_recovers(clue_mod):
+    """An injected scratch limit makes a run fail with CLUE_ERR_OOM before any
+    allocation; the context stays usable for runs that fit."""
+    small = gen.make_event(2000, 4, 1, "blobs")
+    big = gen.make_event(400_000, 100, 2, "blobs")
+    cl = _cl(clue_mod, gen.EXTENT, 100, max_scratch_bytes=40_000_000)
+    cid, _ = cl.run(small.x, small.y, small.layer, small.energy, gen.PARAMS_BLOBS)
+    cl.sync()
+    with pytest.raises(clue_mod.ClueError) as ei:
+        cl.run(big.x, big.y, big.layer, big.energy, gen.PARAMS_BLOBS)
+    assert ei.value.code == clue_mod.CLUE_ERR_OOM
+    cid2, _ = cl.run(small.x, small.y, small.layer, small.energy, gen.PARAMS_BLOBS)
+    cl.sync()
+    assert np.array_equal(cid.cpu().numpy(), cid2.cpu().numpy())
+
+
+def test_unit_weight_partition_invariant_under_permutation(clue_mod):
+    """With unit weights rho is an exact integer, so relabelling the hits only
+    relabels the clusters, on the GPU path."""
+    ev = gen.make_event(300_000, 100, 5, "paper")
+    perm = np.random.default_rng(2).permutation(ev.n)
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    a, _ = cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_PAPER)
+    b, _ = cl.run(ev.x[perm], ev.y[perm], ev.layer[perm], ev.energy[perm], gen.PARAMS_PAPER)
+    cl.sync()
+    a, b = a.cpu().numpy(), b.cpu().numpy()[np.argsort(perm)]
+    # same partition: a bijection between the id sets
+    pairs = set(zip(a.tolist(), b.tolist()))
+    assert len(pairs) == len(set(a.tolist())) == len(set(b.tolist()))
+    assert ((a < 0) == (b < 0)).all()
