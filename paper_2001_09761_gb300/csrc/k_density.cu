@@ -252,22 +252,26 @@ __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
             const float ri = me.z;
             const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
             const Window w = window_of(me.x, me.y, p.rwin_nh, ev);
-            float best = __int_as_float(0x7f800000);  // +inf
-            int bj = INT_MAX;
+            // (d2, j) packed as one unsigned key: d2 >= 0, so its float bits
+            // order like its value; starting at (bits(d_m^2), 0) also folds in
+            // the strict test d2 < d_m^2
+            const unsigned long long none = (unsigned long long)__float_as_uint(p.dm2) << 32;
+            unsigned long long best = none;
             for (int by = w.ly; by <= w.hy; ++by) {
                 const int64_t row = plane + (int64_t)by * ev.nbx;
                 const int e = b.cell_start[row + w.hx + 1];
                 for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
                     const float4 h = sp[u];
-                    const float ru = h.z;
                     const float d2 = sq_dist(me.x, me.y, h.x, h.y);
-                    const int j = id_of(h);
-                    const bool take = (ru > ri) & (d2 < p.dm2) & ((d2 < best) | ((d2 == best) & (j < bj)));
-                    best = take ? d2 : best;
-                    bj = take ? j : bj;
+                    const unsigned long long k =
+                        ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)id_of(h);
+                    best = (h.z > ri && k < best) ? k : best;
                 }
             }
-            b.hr[id_of(me)] = make_float4(ri, best, __int_as_float(bj == INT_MAX ? -1 : bj), 0.0f);
+            const bool found = best != none;
+            b.hr[id_of(me)] = make_float4(
+                ri, found ? __uint_as_float((unsigned)(best >> 32)) : __int_as_float(0x7f800000),
+                __int_as_float(found ? (int)(unsigned)best : -1), 0.0f);
         }
     }
 }
