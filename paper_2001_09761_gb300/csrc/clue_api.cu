@@ -836,7 +836,7 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
         if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune timing");
         return clue_sync(ctx);
     };
-    const float scales[] = {1.0f, 1.5f, 2.0f, 3.0f, 4.0f, 6.0f};
+    const float scales[] = {0.5f, 0.75f, 1.0f, 1.5f, 2.0f, 3.0f, 4.0f, 6.0f};
     const int blocks[] = {128, 256};
     const float user_bin = ctx->opts.bin_size;
     const int user_block = ctx->opts.block_size;

@@ -88,9 +88,9 @@ struct Buffers {
     int32_t *rank;       // [N] arrival rank of the hit in its cell (from the count)
     int32_t *count;      // [C] hits per cell (zeroed per run)
     int32_t *cell_start; // [C + 1]
-    float4 *rec;         // [N] hits grouped by cell, unordered within a cell:
-                         //     x, y, w, id (int bits); aliases hr
-    int32_t *perm;       // [N] scratch of the CTA sorter
+    float4 *rec;         // [N] by hit: x, y, w, local cell (int bits), for the
+                         //     ranking's gather; aliases hr
+    int32_t *perm;       // [N] hit ids grouped by cell, unordered within a cell
     int32_t *tmp;        // [N] scratch for the CTA sorter
     int32_t *big;        // [N / SMALL_SEGMENT + 1] cells queued for the CTA sorter
     float4 *sp;          // [N] hits sorted by (cell, id): x, y, w, id (int bits)

@@ -2,9 +2,10 @@
 //
 // The paper pushes each hit into its bin with an atomic (conflict (i) of
 // Sec. 3), which leaves bin contents in a run-dependent order.  Here the index
-// is a counting sort with a canonical result: hits are counted per cell,
-// cell offsets come from a prefix sum, hits are scattered into their cell's
-// segment, and every segment is then put in ascending hit index.  The sorted
+// is a counting sort with a canonical result: hits are counted per cell (the
+// count's atomic hands each hit its arrival rank), cell offsets come from a
+// prefix sum, hit ids are scattered into their cell's segment, and every
+// segment is then put in ascending hit index.  The sorted
 // copy (x, y, w, id packed in one float4 per hit, one 16-byte load per
 // candidate) makes every later neighbour scan a walk over contiguous memory,
 // and the ascending order inside each cell is what lets the density step sum
@@ -32,6 +33,7 @@ __global__ void __launch_bounds__(256) k_fill_count(Buffers b, Params p) {
             const int local = (l * ev.nby + by) * ev.nbx + bx;
             b.key[g] = local;
             b.rank[g] = atomicAdd(&b.count[ev.cell_off + local], 1);
+            b.rec[g] = make_float4(x, y, w, __int_as_float(local));  // gathered by the ranking
             b.fcount[g] = 0;  // follower counters of the decision step
         }
     }
@@ -53,17 +55,16 @@ cudaError_t launch_scan_cells(const Buffers &b, const LaunchCfg &c, cudaStream_t
                                    (int32_t *)b.scan_partials, c.grid_cap, s, launches);
 }
 
-// --- scatter: every hit into its cell's segment at the rank its count
-// returned (order within a cell is not yet fixed).  The hit travels as one
-// 16-byte record (x, y, w, id): one scattered store, no atomic. --------------
+// --- scatter: every hit's id into its cell's segment at the rank its count
+// returned (order within a cell is not yet fixed); one 4-byte scattered
+// store, no atomic. ---------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fill_scatter(Buffers b) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int64_t coff = b.events[tl.event].cell_off;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int g = tl.start + k;
-            const int slot = b.cell_start[coff + b.key[g]] + b.rank[g];
-            b.rec[slot] = make_float4(b.x[g], b.y[g], b.w[g], __int_as_float(g));
+            b.perm[b.cell_start[coff + b.key[g]] + b.rank[g]] = g;
         }
     }
 }
@@ -85,16 +86,16 @@ __global__ void __launch_bounds__(256) k_fill_canon(Buffers b) {
         const int ev_nbxy = ev.nbx * ev.nby;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int pos = tl.start + k;
-            const float4 r = b.rec[pos];
-            const int g = __float_as_int(r.w);
-            const int local = b.key[g];
+            const int g = b.perm[pos];
+            const float4 r = b.rec[g];  // x, y, w, cell of hit g: one 16-byte gather
+            const int local = __float_as_int(r.w);
             const int64_t c = coff + local;
             const int a = b.cell_start[c], e = b.cell_start[c + 1];
             if (e - a <= SMALL_SEGMENT) {
                 int rank = 0;
-                for (int q = a; q < e; ++q) rank += (__float_as_int(b.rec[q].w) < g);
+                for (int q = a; q < e; ++q) rank += (b.perm[q] < g);
                 const int dst = a + rank;
-                b.sp[dst] = r;
+                b.sp[dst] = make_float4(r.x, r.y, r.z, __int_as_float(g));
                 b.lay_s[dst] = local / ev_nbxy;
             } else if (pos == a) {
                 const int i = atomicAdd(&b.ctrl->nbig, 1);
@@ -111,9 +112,9 @@ cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t
 }
 
 // --- CTA sorter for long segments: a stable least-significant-digit radix
-// sort (8-bit digits) of the segment's hit ids, read from the slot records
-// and then passed between `tmp` and `perm` (both hold the segment at the same
-// offsets, so no memory is shared between segments).  Stability within a chunk comes from warp match masks,
+// sort (8-bit digits) of the segment's hit ids, passed between `perm` and
+// `tmp` (both hold the segment at the same offsets, so no memory is shared
+// between segments).  Stability within a chunk comes from warp match masks,
 // across chunks from processing them in order. ---------------------------------
 constexpr int BIG_THREADS = 256;
 constexpr int BIG_WARPS = BIG_THREADS / 32;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_fill_big(Buffers b) {
         // layer of the cell: the event is that of any hit in the segment
         int lay;
         {
-            const int g0 = __float_as_int(b.rec[a].w);
+            const int g0 = b.perm[a];
             int lo = 0, hi = b.nevents - 1;  // event of g0 by bisection on hit_off
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_fill_big(Buffers b) {
         // range of ids in the segment
         int vmin = 0x7fffffff, vmax = 0;
         for (int i = tid; i < h; i += BIG_THREADS) {
-            const int v = __float_as_int(b.rec[a + i].w);
+            const int v = b.perm[a + i];
             vmin = min(vmin, v);
             vmax = max(vmax, v);
         }
@@ -167,14 +168,15 @@ __global__ void __launch_bounds__(BIG_THREADS) k_fill_big(Buffers b) {
         const unsigned range = (unsigned)(vmax - vmin);
         const int bits = range ? 32 - __clz(range) : 1;
         const int passes = (bits + 7) / 8;
-        // pass 0 reads the records' ids (absolute); later passes ping-pong
-        // relative ids between tmp and perm
-        const float4 *rec = b.rec + a;
+        // pass 0 reads absolute ids from perm; later passes ping-pong relative
+        // ids between tmp and perm (the whole segment is read before the
+        // second pass writes perm)
+        const int *ids0 = b.perm + a;
         int *src = nullptr, *dst = b.tmp + a, *other = b.perm + a;
         for (int pass = 0; pass < passes; ++pass) {
             const int shift = 8 * pass;
             const int sub = pass == 0 ? vmin : 0;
-#define SRC(i) (pass == 0 ? __float_as_int(rec[(i)].w) : src[(i)])
+#define SRC(i) (pass == 0 ? ids0[(i)] : src[(i)])
             hist[tid] = 0;
             for (int w = 0; w < BIG_WARPS; ++w) wcount[w][tid] = 0;
             __syncthreads();
