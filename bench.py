@@ -175,9 +175,8 @@ ALG_BYTES = {
     "fill_scatter": 4 + 4 + 4 + 12 + 16,  # cell, rank, cell start, x/y/w in; record out
     "fill_canon": 16 + 4 + 8 + 16 + 4,  # record, cell, cell range in; sorted hit, layer out
     "rho": 16 + 4 + 4,                 # x, y, w, id, layer in; rho out
-    "nh_delta": 16 + 4 + 4 + 12,       # x, y, id, rho, layer in; rho, delta^2, nh out
-    "decide": 12 + 1,                  # rho, delta^2, nh in; flags out
-    "link": 1 + 8 + 4 + 4 + 1,         # flags, prefix, nh in; id, seed flag out
+    "nh_delta": 16 + 4 + 4 + 4,        # x, y, id, rho, layer in; decision code out
+    "link": 4 + 8 + 4 + 1,             # code, prefix in; id, seed flag out
     "chase": 4 + 4 + 4,                # id, nh in; id out
     "expand_level": 8 + 4 + 4 + 4,     # list range, parent id, follower in; id out
     "complete": 4 + 4,                 # id in, id out

@@ -227,7 +227,7 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     b.rec = (float4 *)take(n * 16);
     b.hr = b.rec;
     b.spr = (float4 *)take(n * 16);
-    b.flags = (uint8_t *)take(n);
+    b.code = b.key;  // the cell of each hit is dead once the ids are scattered
     b.fcount = (int32_t *)take(n * 4);
     b.hs = (unsigned long long *)take((n + 1) * 8);
     b.fol = (int32_t *)take(n * 4);
@@ -363,8 +363,6 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(rec("rho"));
     CK(launch_nh(b, p, cfg, s));
     CK(rec("nh_delta"));
-    CK(launch_decide(b, p, cfg, s));
-    CK(rec("decide"));
     CK(launch_scan_hits(b, cfg, s, &nl));
     CK(rec("scan_hits"));
     CK(launch_link(b, p, cfg, s));
@@ -372,7 +370,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     if (p.chase) {
         CK(launch_chase(b, cfg, s));
         CK(rec("chase"));
-        nl += 5;  // rho, nh, decide, link, chase
+        nl += 4;  // rho, nh (with the decision), link, chase
     } else {
         for (int level = 0; level < EXPAND_LEVELS; ++level) {
             CK(launch_expand_level(b, cfg, level, s));
@@ -380,7 +378,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
         }
         CK(launch_complete(b, cfg, s));
         CK(rec("complete"));
-        nl += 5 + EXPAND_LEVELS;  // rho, nh, decide, link, complete, levels
+        nl += 4 + EXPAND_LEVELS;  // rho, nh, link, complete, levels
     }
     *launches = nl;
     return CLUE_OK;

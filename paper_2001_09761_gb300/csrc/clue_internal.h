@@ -17,8 +17,9 @@ constexpr int SMALL_SEGMENT = 128;
 // cluster id of a follower whose id has not been passed down yet.
 constexpr int32_t PENDING = -2;
 
-// flag bits of a hit after the decision step
-constexpr uint8_t F_SEED = 1, F_OUTLIER = 2, F_FOLLOWER = 4;
+// Outcome of the decision step per hit (Sec. 2.2): a follower stores its
+// nearest-higher (>= 0); otherwise one of these codes.
+constexpr int32_t CODE_NOISE = -1, CODE_SEED = -2, CODE_OUTLIER = -3;
 
 // Error bits raised on the device (ctrl->err).
 constexpr unsigned ERRBIT_INPUT = 1u, ERRBIT_TIMEOUT = 2u;
@@ -97,9 +98,10 @@ struct Buffers {
     int32_t *lay_s;      // [N] layer in sorted order
     // density
     float4 *spr;         // [N] sorted order: x, y, rho, id (written by the rho step)
-    float4 *hr;          // [N] by hit: rho, delta^2, nh (int bits: batch index or -1)
+    float4 *hr;          // [N] by sorted position: rho, delta^2, nh (int bits: batch
+                         //     index or -1), read only by the intermediates export
     // decision / expansion
-    uint8_t *flags;      // [N]
+    int32_t *code;       // [N] by hit: nh for a follower, else CODE_*; aliases key
     int32_t *fcount;     // [N] followers per hit (zeroed in the fill step)
     int32_t *frank;      // [N] arrival rank of a follower in its nh's list (aliases rank)
     unsigned long long *hs;  // [N + 1] exclusive scan of (seed << 32 | followers)
@@ -128,7 +130,6 @@ cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t
 cudaError_t launch_fill_big(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_decide(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_chase(const Buffers &b, const LaunchCfg &c, cudaStream_t s);

@@ -40,7 +40,7 @@ constexpr size_t STATIC_BYTES =
     al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ + al((NB / SMALL_SEGMENT + 1) * 4) /*big*/ +
     al(NB * 16) /*sp*/ + al(NB * 4) /*lay_s*/ +
     al(NB * 16) /*rec = hr*/ + al(NB * 16) /*spr*/ +
-    al(NB) /*flags*/ + al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
+    al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
     al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/;
 
 }  // namespace
@@ -141,7 +141,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.rec = (float4 *)take(NB * 16);
     b.hr = b.rec;
     b.spr = (float4 *)take(NB * 16);
-    b.flags = (uint8_t *)take(NB);
+    b.code = b.key;
     b.fcount = (int32_t *)take(NB * 4);
     b.hs = (unsigned long long *)take((NB + 1) * 8);
     b.fol = (int32_t *)take(NB * 4);
@@ -225,7 +225,6 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     SCK(launch_fill_big(b, cfg, s));
     SCK(launch_rho(b, prm, cfg, s));
     SCK(launch_nh(b, prm, cfg, s));
-    SCK(launch_decide(b, prm, cfg, s));
     SCK(launch_scan_hits(b, cfg, s, &nl));
     SCK(launch_link(b, prm, cfg, s));
     SCK(launch_expand(b, cfg, s));

@@ -1,5 +1,6 @@
-// Steps S4 and S5: seed / outlier decision with follower lists (Sec. 2.2,
-// Eq. 5, Algorithm 3) and the expansion of cluster ids down the followers.
+// Steps S4 and S5: seed ids and follower lists (Sec. 2.2, Eq. 5, Algorithm 3)
+// and the expansion of cluster ids down the followers.  The seed / outlier
+// decision itself is taken by the nh step, which stores one code per hit.
 //
 // The paper appends seeds and followers with atomics (conflicts (ii) and (iii)
 // of Sec. 3), so seed numbering depends on thread timing.  Here seed ids are
@@ -13,41 +14,18 @@
 
 namespace clue {
 
-__global__ void __launch_bounds__(256) k_decide(Buffers b, Params p) {
-    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-        const Tile tl = b.tiles[t];
-        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-            const int g = tl.start + k;
-            const float4 h = b.hr[g];
-            const float r = h.x, d2 = h.y;
-            const int j = __float_as_int(h.z);
-            const bool seed = (r > p.rhoc) && (d2 > p.dcs2);
-            const bool outl = (r < p.rhoc) && (d2 > p.dos2);
-            const bool fol = !seed && !outl && j >= 0;
-            b.flags[g] = (seed ? F_SEED : 0) | (outl ? F_OUTLIER : 0) | (fol ? F_FOLLOWER : 0);
-            if (fol && !p.chase) b.frank[g] = atomicAdd(&b.fcount[j], 1);
-        }
-    }
-}
-
-cudaError_t launch_decide(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
-    const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
-    k_decide<<<grid > 0 ? grid : 1, c.block_fill, 0, s>>>(b, p);
-    return cudaGetLastError();
-}
-
 // (is_seed << 32 | follower count): one scan gives both the global seed rank
 // (high word) and the follower-list offset (low word) of every hit.
 struct LoadPacked {
-    const uint8_t *flags;
+    const int32_t *code;
     const int32_t *fcount;
     __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
-        return ((unsigned long long)(flags[i] & F_SEED) << 32) | (unsigned)fcount[i];
+        return ((unsigned long long)(code[i] == CODE_SEED) << 32) | (unsigned)fcount[i];
     }
 };
 
 cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches) {
-    return exclusive_scan<unsigned long long>(LoadPacked{b.flags, b.fcount}, b.N, b.hs,
+    return exclusive_scan<unsigned long long>(LoadPacked{b.code, b.fcount}, b.N, b.hs,
                                               (unsigned long long *)b.scan_partials, c.grid_cap,
                                               s, launches);
 }
@@ -69,19 +47,16 @@ __global__ void __launch_bounds__(256) k_link(Buffers b, Params p) {
             int root = 0;
             if (k < tl.len) {
                 const int g = tl.start + k;
-                const uint8_t f = b.flags[g];
-                if (f & F_SEED) {
+                const int code = b.code[g];
+                if (code == CODE_SEED) {
                     const unsigned long long hg = b.hs[g];
                     b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);
                     b.is_seed[g] = 1;
                     root = (unsigned)b.hs[g + 1] != (unsigned)hg;  // has followers
                 } else {
                     b.is_seed[g] = 0;
-                    if (f & F_FOLLOWER) {
-                        if (!p.chase) {
-                            const int j = __float_as_int(b.hr[g].z);
-                            b.fol[(int)(unsigned)b.hs[j] + b.frank[g]] = g;
-                        }
+                    if (code >= 0) {  // a follower of nh = code
+                        if (!p.chase) b.fol[(int)(unsigned)b.hs[code] + b.frank[g]] = g;
                         b.cid[g] = PENDING;
                     } else {
                         b.cid[g] = -1;
@@ -124,7 +99,7 @@ __global__ void __launch_bounds__(256, 2) k_chase(Buffers b) {
             for (int u = 0; u < U; ++u) {
                 const int k = k0 + u * (int)blockDim.x;
                 act[u] = k < tl.len && b.cid[tl.start + k] == PENDING;
-                v[u] = act[u] ? __float_as_int(b.hr[tl.start + k].z) : 0;
+                v[u] = act[u] ? b.code[tl.start + k] : 0;  // a pending hit is a follower
                 cv[u] = PENDING;
             }
             int64_t steps = 0;
@@ -137,7 +112,7 @@ __global__ void __launch_bounds__(256, 2) k_chase(Buffers b) {
 #pragma unroll
                 for (int u = 0; u < U; ++u)
                     if (act[u] && cv[u] == PENDING) {
-                        v[u] = __float_as_int(b.hr[v[u]].z);
+                        v[u] = b.code[v[u]];
                         any = true;
                     }
                 ++steps;
@@ -258,11 +233,11 @@ __global__ void __launch_bounds__(256) k_complete(Buffers b) {
                 b.cid[g] = -1;
                 continue;
             }
-            int v = __float_as_int(b.hr[g].z);
+            int v = b.code[g];
             int cv = b.cid[v];
             int64_t steps = 0;
             while (cv == PENDING && steps < b.N) {
-                v = __float_as_int(b.hr[v].z);
+                v = b.code[v];
                 cv = b.cid[v];
                 ++steps;
             }
@@ -281,13 +256,16 @@ cudaError_t launch_complete(const Buffers &b, const LaunchCfg &c, cudaStream_t s
     return cudaGetLastError();
 }
 
+// Intermediates for tests: the nh step's record is in sorted order; each
+// sorted position writes its hit's entries.
 __global__ void __launch_bounds__(256) k_export(Buffers b, float *rho, float *delta, int32_t *nh) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int64_t hoff = b.events[tl.event].hit_off;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-            const int g = tl.start + k;
-            const float4 h = b.hr[g];
+            const int q = tl.start + k;
+            const int g = __float_as_int(b.sp[q].w);
+            const float4 h = b.hr[q];
             if (rho) rho[g] = h.x;
             if (delta) delta[g] = sqrtf(h.y);
             if (nh) {

@@ -237,9 +237,11 @@ cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cu
 }
 
 // nh_i: over the window of radius d_m, the (d2, j)-lexicographic minimum among
-// hits with d2 < d_m^2 and rho_j > rho_i (the minimum is order-free).  Writes
-// rho, delta^2 and nh back by hit index as one 16-byte record (one scattered
-// store per hit; separate 4-byte stores cost three).
+// hits with d2 < d_m^2 and rho_j > rho_i (the minimum is order-free).  The
+// same thread takes the seed / outlier decision (Sec. 2.2), which needs only
+// this hit's rho, delta and nh, and stores one 4-byte code by hit (the
+// scattered store this step cannot avoid); rho, delta^2, nh also go, in
+// sorted order (coalesced), to a record the intermediates export reads.
 __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
     const float4 *__restrict__ sp = b.spr;  // x, y, rho, id
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
@@ -269,9 +271,18 @@ __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
                 }
             }
             const bool found = best != none;
-            b.hr[id_of(me)] = make_float4(
-                ri, found ? __uint_as_float((unsigned)(best >> 32)) : __int_as_float(0x7f800000),
-                __int_as_float(found ? (int)(unsigned)best : -1), 0.0f);
+            const float d2v = found ? __uint_as_float((unsigned)(best >> 32))
+                                    : __int_as_float(0x7f800000);  // +inf (Eq. 4)
+            const int nhj = found ? (int)(unsigned)best : -1;
+            b.hr[q] = make_float4(ri, d2v, __int_as_float(nhj), 0.0f);
+            // the decision of Sec. 2.2 needs only this hit's rho, delta and nh:
+            // seed, outlier, or a follower of nh (Algorithm 3), stored by hit
+            const bool seed = (ri > p.rhoc) && (d2v > p.dcs2);
+            const bool outl = (ri < p.rhoc) && (d2v > p.dos2);
+            const int code = seed ? CODE_SEED : outl ? CODE_OUTLIER : (nhj >= 0 ? nhj : CODE_NOISE);
+            const int g = id_of(me);
+            b.code[g] = code;
+            if (!p.chase && code >= 0) b.frank[g] = atomicAdd(&b.fcount[code], 1);
         }
     }
 }
