@@ -230,6 +230,7 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     b.code = b.key;  // the cell of each hit is dead once the ids are scattered
     b.fcount = (int32_t *)take(n * 4);
     b.hs = (unsigned long long *)take((n + 1) * 8);
+    b.srank = (int32_t *)b.hs;
     b.fol = (int32_t *)take(n * 4);
     b.seed_list = (int32_t *)take(n * 4);
     b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
@@ -363,7 +364,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(rec("rho"));
     CK(launch_nh(b, p, cfg, s));
     CK(rec("nh_delta"));
-    CK(launch_scan_hits(b, cfg, s, &nl));
+    CK(launch_scan_hits(b, p, cfg, s, &nl));
     CK(rec("scan_hits"));
     CK(launch_link(b, p, cfg, s));
     CK(rec("link"));

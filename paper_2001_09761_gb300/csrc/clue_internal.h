@@ -105,6 +105,7 @@ struct Buffers {
     int32_t *fcount;     // [N] followers per hit (zeroed in the fill step)
     int32_t *frank;      // [N] arrival rank of a follower in its nh's list (aliases rank)
     unsigned long long *hs;  // [N + 1] exclusive scan of (seed << 32 | followers)
+    int32_t *srank;      // [N + 1] exclusive scan of seed flags (chase mode; aliases hs)
     int32_t *fol;        // [N] follower lists (CSR by nh)
     int32_t *seed_list;  // [N] seeds by global seed rank
     int32_t *front_a;    // [N] expansion frontiers (alias perm / tmp, free after S1)
@@ -130,7 +131,8 @@ cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t
 cudaError_t launch_fill_big(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
+cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s,
+                             int *launches);
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_chase(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);  // all levels

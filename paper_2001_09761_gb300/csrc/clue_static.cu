@@ -144,6 +144,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.code = b.key;
     b.fcount = (int32_t *)take(NB * 4);
     b.hs = (unsigned long long *)take((NB + 1) * 8);
+    b.srank = (int32_t *)b.hs;
     b.fol = (int32_t *)take(NB * 4);
     b.seed_list = (int32_t *)take(NB * 4);
     b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
@@ -225,7 +226,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     SCK(launch_fill_big(b, cfg, s));
     SCK(launch_rho(b, prm, cfg, s));
     SCK(launch_nh(b, prm, cfg, s));
-    SCK(launch_scan_hits(b, cfg, s, &nl));
+    SCK(launch_scan_hits(b, prm, cfg, s, &nl));
     SCK(launch_link(b, prm, cfg, s));
     SCK(launch_expand(b, cfg, s));
     SCK(launch_complete(b, cfg, s));

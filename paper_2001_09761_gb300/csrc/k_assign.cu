@@ -24,7 +24,19 @@ struct LoadPacked {
     }
 };
 
-cudaError_t launch_scan_hits(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches) {
+// Chase mode needs no follower lists: the seed ranks alone, as 32-bit values.
+struct LoadSeed {
+    const int32_t *code;
+    __device__ __forceinline__ int32_t operator()(int64_t i) const {
+        return code[i] == CODE_SEED;
+    }
+};
+
+cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c,
+                             cudaStream_t s, int *launches) {
+    if (p.chase)
+        return exclusive_scan<int32_t>(LoadSeed{b.code}, b.N, b.srank,
+                                       (int32_t *)b.scan_partials, c.grid_cap, s, launches);
     return exclusive_scan<unsigned long long>(LoadPacked{b.code, b.fcount}, b.N, b.hs,
                                               (unsigned long long *)b.scan_partials, c.grid_cap,
                                               s, launches);
@@ -41,7 +53,7 @@ __global__ void __launch_bounds__(256) k_link(Buffers b, Params p) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int64_t hoff = b.events[tl.event].hit_off;
-        const unsigned ebase = (unsigned)(b.hs[hoff] >> 32);
+        const unsigned ebase = p.chase ? (unsigned)b.srank[hoff] : (unsigned)(b.hs[hoff] >> 32);
         for (int k0 = 0; k0 < tl.len; k0 += blockDim.x) {
             const int k = k0 + threadIdx.x;
             int root = 0;
@@ -49,10 +61,14 @@ __global__ void __launch_bounds__(256) k_link(Buffers b, Params p) {
                 const int g = tl.start + k;
                 const int code = b.code[g];
                 if (code == CODE_SEED) {
-                    const unsigned long long hg = b.hs[g];
-                    b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);
+                    if (p.chase) {
+                        b.cid[g] = (int32_t)((unsigned)b.srank[g] - ebase);
+                    } else {
+                        const unsigned long long hg = b.hs[g];
+                        b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);
+                        root = (unsigned)b.hs[g + 1] != (unsigned)hg;  // has followers
+                    }
                     b.is_seed[g] = 1;
-                    root = (unsigned)b.hs[g + 1] != (unsigned)hg;  // has followers
                 } else {
                     b.is_seed[g] = 0;
                     if (code >= 0) {  // a follower of nh = code

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) k_fill_count(Buffers b, Params p) {
             b.key[g] = local;
             b.rank[g] = atomicAdd(&b.count[ev.cell_off + local], 1);
             b.rec[g] = make_float4(x, y, w, __int_as_float(local));  // gathered by the ranking
-            b.fcount[g] = 0;  // follower counters of the decision step
+            if (!p.chase) b.fcount[g] = 0;  // follower counters of the follower lists
         }
     }
 }
