@@ -172,12 +172,12 @@ def run_reference(args):
 # the stage's own outputs).
 ALG_BYTES = {
     "fill_count": 16 + 4 + 4 + 4,      # x, y, w, layer in; cell, rank, cell count out
-    "fill_scatter": 4 + 4 + 4 + 12 + 16,  # cell, rank, cell start, x/y/w in; record out
-    "fill_canon": 16 + 4 + 8 + 16 + 4,  # record, cell, cell range in; sorted hit, layer out
+    "fill_scatter": 4 + 4 + 4 + 4,     # cell, rank, cell start in; hit id out
+    "fill_canon": 4 + 16 + 8 + 16 + 4,  # id, packed record, cell range in; sorted hit, layer out
     "rho": 16 + 4 + 4,                 # x, y, w, id, layer in; rho out
-    "nh_delta": 16 + 4 + 4 + 4,        # x, y, id, rho, layer in; decision code out
-    "link": 4 + 8 + 4 + 1,             # code, prefix in; id, seed flag out
-    "chase": 4 + 4 + 4,                # id, nh in; id out
+    "nh_delta": 16 + 4 + 4 + 8,        # x, y, rho, id, layer in; code, (delta^2, nh) out
+    "link": 4 + 4 + 4 + 1,             # code, seed rank in; id, seed flag out
+    "chase": 4 + 4 + 4,                # code, id in; id out
     "expand_level": 8 + 4 + 4 + 4,     # list range, parent id, follower in; id out
     "complete": 4 + 4,                 # id in, id out
 }
@@ -390,12 +390,16 @@ def main():
     stop = torch.cuda.Event(enable_timing=True)
     start.record(cl.stream)
     launches = 0
-    for _ in range(args.steps):
+    for i in range(args.steps):
         cl.run_batch(tx, ty, tl, te, offs, PARAMS, out=(cid, seed))
         launches += cl.launch_count()
-        for k, v in cl.kernel_times().items():  # waits for this step's events
-            kern[k] = kern.get(k, 0.0) + v
+        if i:  # the previous step's kernel times, while this step runs
+            for k, v in cl.kernel_times(back=1).items():
+                kern[k] = kern.get(k, 0.0) + v
     stop.record(cl.stream)
+    if args.steps:
+        for k, v in cl.kernel_times().items():
+            kern[k] = kern.get(k, 0.0) + v
     stop.synchronize()
     torch.cuda.synchronize()
     if dist:

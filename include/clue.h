@@ -159,6 +159,19 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
                         float dc, float rhoc, float delta_c, float delta_o,
                         int32_t *cluster_id, uint8_t *is_seed);
 
+/*
+ * Queue the copies of one event's inputs, n hits of the arrays x, y, layer,
+ * energy (host or device; pinned host memory gives asynchronous copies, and
+ * pageable host memory may be reused once the call returns), into the DEVICE
+ * arrays dx, dy, dlayer, denergy at element offset `offset`, on `stream`
+ * (cudaStream_t; NULL = legacy default stream).  For servers that stage
+ * events into a resident batch buffer as they arrive (one call instead of
+ * four).  No context needed.  Errors: CLUE_ERR_ARG, CLUE_ERR_CUDA.
+ */
+int clue_stage_event(const float *x, const float *y, const int32_t *layer,
+                     const float *energy, int64_t n, float *dx, float *dy, int32_t *dlayer,
+                     float *denergy, int64_t offset, void *stream);
+
 /* Wait for the context's queued work; returns the first deferred error
  * (CLUE_ERR_INPUT, CLUE_ERR_TIMEOUT, CLUE_ERR_CUDA) or CLUE_OK, and clears it. */
 int clue_sync(clue_ctx *ctx);
@@ -197,13 +210,18 @@ int clue_set_tuning(clue_ctx *ctx, const char *text);
 
 /* Per-kernel timing: when on (1), the next runs record a CUDA event before
  * the first kernel and after each kernel (or launch group: a prefix sum's
- * three kernels count as one).  clue_stage_times waits for the last run and
- * writes up to `cap` durations in ms, in launch order, and their names
- * (comma-separated, into names if not NULL, capacity names_cap); it returns
- * the number of entries, or a negative CLUE_ERR_* code (-CLUE_ERR_STATE when
- * no profiled run exists). */
+ * three kernels count as one).  clue_stage_times waits for the last profiled
+ * run and writes up to `cap` durations in ms, in launch order, and their
+ * names (comma-separated, into names if not NULL, capacity names_cap); it
+ * returns the number of entries, or a negative CLUE_ERR_* code
+ * (-CLUE_ERR_STATE when no profiled run exists).  clue_stage_times_back does
+ * the same for the profiled run `back` runs before the last (0 = the last;
+ * the last 4 profiled runs stay readable), so a caller can read a run's times
+ * while later runs are queued, without draining the stream each run. */
 int clue_set_profiling(clue_ctx *ctx, int32_t on);
 int clue_stage_times(clue_ctx *ctx, float *ms, int32_t cap, char *names, int64_t names_cap);
+int clue_stage_times_back(clue_ctx *ctx, int32_t back, float *ms, int32_t cap, char *names,
+                          int64_t names_cap);
 
 /* Number of kernels the last run launched (for launch accounting). */
 int32_t clue_last_launch_count(clue_ctx *ctx);

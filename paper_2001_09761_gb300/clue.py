@@ -27,8 +27,8 @@ ABI_SYMBOLS = [
     "clue_default_opts", "clue_create", "clue_destroy", "clue_set_stream", "clue_run",
     "clue_run_batch", "clue_run_batch_host", "clue_sync", "clue_get_intermediates",
     "clue_autotune", "clue_get_tuning", "clue_set_tuning", "clue_set_profiling",
-    "clue_stage_times", "clue_last_launch_count", "clue_scratch_bytes", "clue_strerror",
-    "clue_last_message", "clue_version", "clue_run_static",
+    "clue_stage_times", "clue_stage_times_back", "clue_last_launch_count", "clue_scratch_bytes", "clue_strerror",
+    "clue_last_message", "clue_version", "clue_run_static", "clue_stage_event",
 ]
 
 
@@ -85,6 +85,7 @@ def load(path: os.PathLike | None = None):
         "clue_set_tuning": (ctypes.c_int, [P, ctypes.c_char_p]),
         "clue_set_profiling": (ctypes.c_int, [P, I32]),
         "clue_stage_times": (ctypes.c_int, [P, P, I32, ctypes.c_char_p, I64]),
+        "clue_stage_times_back": (ctypes.c_int, [P, I32, P, I32, ctypes.c_char_p, I64]),
         "clue_last_launch_count": (I32, [P]),
         "clue_scratch_bytes": (I64, [P]),
         "clue_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -92,6 +93,7 @@ def load(path: os.PathLike | None = None):
         "clue_version": (ctypes.c_char_p, []),
         "clue_run_static": (ctypes.c_int, [P, P, P, P, I64, F, F, F, F, F, F, F, F, I32, P, P,
                                            P]),
+        "clue_stage_event": (ctypes.c_int, [P, P, P, P, I64, P, P, P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -156,6 +158,11 @@ def clue_run_batch_host(ctx, x, y, layer, energy, offsets, n_events, dc, rhoc, d
                                       delta_c, delta_o, cluster_id, is_seed)
 
 
+def clue_stage_event(x, y, layer, energy, n, dx, dy, dlayer, denergy, offset, stream) -> int:
+    return load().clue_stage_event(x, y, layer, energy, n, dx, dy, dlayer, denergy, offset,
+                                   stream)
+
+
 def clue_sync(ctx) -> int:
     return load().clue_sync(ctx)
 
@@ -186,13 +193,14 @@ def clue_set_profiling(ctx, on: bool) -> int:
     return load().clue_set_profiling(ctx, 1 if on else 0)
 
 
-def clue_stage_times(ctx):
-    """[(kernel name, ms), ...] of the last profiled run, in launch order."""
+def clue_stage_times(ctx, back=0):
+    """[(kernel name, ms), ...] of the profiled run `back` runs before the
+    last one (0 = the last), in launch order."""
     ms = (ctypes.c_float * 64)()
     names = ctypes.create_string_buffer(2048)
-    n = load().clue_stage_times(ctx, ms, 64, names, 2048)
+    n = load().clue_stage_times_back(ctx, int(back), ms, 64, names, 2048)
     if n < 0:
-        raise ClueError(-n, "clue_stage_times")
+        raise ClueError(-n, "clue_stage_times_back")
     return list(zip(names.value.decode().split(","), list(ms)[:n]))
 
 
@@ -393,10 +401,11 @@ class Clusterer:
     def set_profiling(self, on=True):
         _check(clue_set_profiling(self.ctx, on), "clue_set_profiling", self.ctx)
 
-    def kernel_times(self):
-        """{kernel: ms} of the last profiled run (repeated launches summed)."""
+    def kernel_times(self, back=0):
+        """{kernel: ms} of the last profiled run, or of the one `back` runs
+        before it (repeated launches summed)."""
         out = {}
-        for k, v in clue_stage_times(self.ctx):
+        for k, v in clue_stage_times(self.ctx, back):
             out[k] = out.get(k, 0.0) + v
         return out
 

@@ -28,6 +28,7 @@ namespace {
 constexpr int NCLASS = 5;
 constexpr int64_t CLASS_EDGE[NCLASS + 1] = {0, 32768, 100000, 316228, 1000000, INT64_MAX};
 constexpr int NPROF = 40;  // profiling events: one before the first kernel, one after each group
+constexpr int NPSETS = 4;  // profiled runs whose times stay readable (a ring of event sets)
 constexpr int NSTAGING = 4;
 constexpr size_t GRAPH_CACHE_MAX = 16;
 constexpr int64_t MAX_HITS = 2147483646LL;
@@ -41,6 +42,9 @@ int class_of(int64_t n) {
 struct GraphEntry {
     uint64_t sig = 0;
     cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;  // kept while profiled: its event-record nodes
+    std::vector<cudaGraphNode_t> evnodes;  // node stamping profiling event k
+    std::vector<const char *> prof_names;
     void *dtables = nullptr;
     Buffers buf{};
     LaunchCfg cfg{};
@@ -92,9 +96,11 @@ struct clue_ctx {
     float bin_scale[NCLASS];
     int block_density = 256;
     bool profiling = false;
-    bool prof_recorded = false;
-    cudaEvent_t pev[NPROF] = {};
-    std::vector<const char *> prof_names;  // name of the kernel(s) ending at pev[i + 1]
+    // ring of event sets: profiled run r stamps set r % NPSETS
+    cudaEvent_t pev[NPSETS][NPROF] = {};
+    std::vector<const char *> prof_names[NPSETS];  // kernel(s) ending at pev[s][i + 1]
+    int prof_set = 0;    // the set the next profiled run stamps
+    int prof_count = 0;  // profiled runs so far, capped at NPSETS
     Buffers last{};
     LaunchCfg last_cfg{};
     bool have_last = false;
@@ -223,9 +229,9 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     b.sp = (float4 *)take(n * 16);
     b.lay_s = (int32_t *)take(n * 4);
     // one 16-byte-per-hit region: the grid fill's slot records, then (after
-    // the fill) the per-hit records rho, delta^2, nh of the nh step
+    // the fill) the per-hit records delta^2, nh of the nh step (8 bytes each)
     b.rec = (float4 *)take(n * 16);
-    b.hr = b.rec;
+    b.hr = (float2 *)b.rec;
     b.spr = (float4 *)take(n * 16);
     b.code = b.key;  // the cell of each hit is dead once the ids are scattered
     b.fcount = (int32_t *)take(n * 4);
@@ -245,6 +251,7 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
 void drop_graphs(clue_ctx *ctx) {
     for (auto &g : ctx->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
         if (g.dtables) cudaFree(g.dtables);
     }
     ctx->graphs.clear();
@@ -326,10 +333,11 @@ LaunchCfg make_cfg(const clue_ctx *ctx) {
 }
 
 // Queue the whole pipeline (S1 grid fill .. S5 expansion) on ctx->stream.
-// With profiling on, an event is recorded before the first kernel and after
-// each launch group, named in ctx->prof_names.
+// With profiling on, an event of the current set is recorded before the first
+// kernel and after each launch group, named in ctx->prof_names.
 int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &cfg,
             int *launches) {
+    const int set = ctx->prof_set;
     cudaStream_t s = ctx->stream;
     int nl = 0;
     const bool prof = ctx->profiling;
@@ -340,11 +348,11 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     const unsigned rec_flags =
         cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     int ev = 0;
-    ctx->prof_names.clear();
+    ctx->prof_names[set].clear();
     auto rec = [&](const char *name) -> cudaError_t {
         if (!prof) return cudaSuccess;
-        if (name) ctx->prof_names.push_back(name);
-        return cudaEventRecordWithFlags(ctx->pev[ev++], s, rec_flags);
+        if (name) ctx->prof_names[set].push_back(name);
+        return cudaEventRecordWithFlags(ctx->pev[set][ev++], s, rec_flags);
     };
     CK(cudaMemsetAsync(&b.ctrl->overflow, 0, sizeof(Ctrl) - sizeof(unsigned), s));
     CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
@@ -382,6 +390,48 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
         nl += 4 + EXPAND_LEVELS;  // rho, nh, link, complete, levels
     }
     *launches = nl;
+    return CLUE_OK;
+}
+
+// A run was queued: with profiling on, its event set becomes the newest one.
+void prof_advance(clue_ctx *ctx) {
+    if (!ctx->profiling) return;
+    ctx->prof_set = (ctx->prof_set + 1) % NPSETS;
+    ctx->prof_count = std::min(ctx->prof_count + 1, NPSETS);
+}
+
+// Point a captured graph's event-record nodes at the current event set (an
+// update of the executable graph; launches already queued keep their events).
+int graph_use_set(clue_ctx *ctx, GraphEntry &g) {
+    const int set = ctx->prof_set;
+    for (size_t k = 0; k < g.evnodes.size(); ++k)
+        CK(cudaGraphExecEventRecordNodeSetEvent(g.exec, g.evnodes[k], ctx->pev[set][k]));
+    ctx->prof_names[set] = g.prof_names;
+    return CLUE_OK;
+}
+
+// After capture: the node that stamps each profiling event of the set used.
+int find_event_nodes(clue_ctx *ctx, GraphEntry &g, int nev) {
+    size_t nn = 0;
+    CK(cudaGraphGetNodes(g.graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(cudaGraphGetNodes(g.graph, nodes.data(), &nn));
+    g.evnodes.assign(nev, nullptr);
+    const int set = ctx->prof_set;
+    for (auto n : nodes) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(n, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        CK(cudaGraphEventRecordNodeGetEvent(n, &ev));
+        for (int k = 0; k < nev; ++k)
+            if (ctx->pev[set][k] == ev) g.evnodes[k] = n;
+    }
+    for (auto n : g.evnodes)
+        if (!n) {
+            ctx->msg = "profiling event missing from the captured graph";
+            return CLUE_ERR_CUDA;
+        }
     return CLUE_OK;
 }
 
@@ -438,13 +488,17 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
         const uint64_t sig = signature(ctx, plan, b, p, cfg);
         for (auto &g : ctx->graphs)
             if (g.sig == sig) {
+                if (ctx->profiling) {
+                    rc = graph_use_set(ctx, g);
+                    if (rc) return rc;
+                }
                 CK(cudaGraphLaunch(g.exec, ctx->stream));
                 g.last_use = ++ctx->tick;
                 ctx->last = g.buf;
                 ctx->last_cfg = g.cfg;
                 ctx->have_last = true;
                 ctx->last_launches = g.launches;
-                ctx->prof_recorded = ctx->profiling;
+                prof_advance(ctx);
                 return CLUE_OK;
             }
         if (ctx->seen.size() > 4096) ctx->seen.clear();  // one-off batches never repeat
@@ -456,6 +510,7 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
                                                return a.last_use < c.last_use;
                                            });
                 cudaGraphExecDestroy(it->exec);
+                if (it->graph) cudaGraphDestroy(it->graph);
                 cudaFree(it->dtables);
                 ctx->graphs.erase(it);
             }
@@ -483,11 +538,24 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
                 if (erc != CLUE_OK && e == cudaSuccess) e = cudaErrorUnknown;
             }
             if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
             if (e != cudaSuccess) {
                 cudaGetLastError();
+                if (graph) cudaGraphDestroy(graph);
                 cudaFree(g.dtables);
                 return cuda_fail(ctx, e, "graph capture");
+            }
+            if (ctx->profiling) {
+                g.graph = graph;
+                g.prof_names = ctx->prof_names[ctx->prof_set];
+                rc = find_event_nodes(ctx, g, (int)g.prof_names.size() + 1);
+                if (rc) {
+                    cudaGraphExecDestroy(g.exec);
+                    cudaGraphDestroy(graph);
+                    cudaFree(g.dtables);
+                    return rc;
+                }
+            } else {
+                cudaGraphDestroy(graph);
             }
             CK(cudaGraphLaunch(g.exec, ctx->stream));
             g.last_use = ++ctx->tick;
@@ -496,7 +564,7 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
             ctx->last_cfg = cfg;
             ctx->have_last = true;
             ctx->last_launches = g.launches;
-            ctx->prof_recorded = ctx->profiling;
+            prof_advance(ctx);
             return CLUE_OK;
         }
     }
@@ -510,7 +578,7 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     ctx->last_cfg = cfg;
     ctx->have_last = true;
     ctx->last_launches = launches;
-    ctx->prof_recorded = ctx->profiling;
+    prof_advance(ctx);
     return CLUE_OK;
 }
 
@@ -581,10 +649,11 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
         e = cudaEventCreateWithFlags(&ctx->staging[i].done, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail(e, "cudaEventCreate");
     }
-    for (int i = 0; i < NPROF; ++i) {
-        e = cudaEventCreate(&ctx->pev[i]);
-        if (e != cudaSuccess) return fail(e, "cudaEventCreate");
-    }
+    for (auto &set : ctx->pev)
+        for (auto &ev : set) {
+            e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return fail(e, "cudaEventCreate");
+        }
     *out = ctx;
     return CLUE_OK;
 }
@@ -603,8 +672,9 @@ void clue_destroy(clue_ctx *ctx) {
         if (s.host) cudaFreeHost(s.host);
         if (s.done) cudaEventDestroy(s.done);
     }
-    for (auto &ev : ctx->pev)
-        if (ev) cudaEventDestroy(ev);
+    for (auto &set : ctx->pev)
+        for (auto &ev : set)
+            if (ev) cudaEventDestroy(ev);
     if (ctx->h2d) {
         cudaStreamSynchronize(ctx->h2d);
         cudaStreamSynchronize(ctx->d2h);
@@ -757,6 +827,22 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
     return clue_sync(ctx);
 }
 
+int clue_stage_event(const float *x, const float *y, const int32_t *layer,
+                     const float *energy, int64_t n, float *dx, float *dy, int32_t *dlayer,
+                     float *denergy, int64_t offset, void *stream) {
+    if (n < 0 || offset < 0) return CLUE_ERR_ARG;
+    if (n == 0) return CLUE_OK;
+    if (!x || !y || !layer || !energy || !dx || !dy || !dlayer || !denergy) return CLUE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n * 4;
+    clue_ctx *ctx = nullptr;  // CK reports without a context
+    CK(cudaMemcpyAsync(dx + offset, x, bytes, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(dy + offset, y, bytes, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(dlayer + offset, layer, bytes, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(denergy + offset, energy, bytes, cudaMemcpyDefault, s));
+    return CLUE_OK;
+}
+
 int clue_get_intermediates(clue_ctx *ctx, float *rho, float *delta, int32_t *nh) {
     if (!ctx) return CLUE_ERR_ARG;
     if (!ctx->have_last) return CLUE_ERR_STATE;
@@ -773,26 +859,34 @@ int clue_set_profiling(clue_ctx *ctx, int32_t on) {
     return CLUE_OK;
 }
 
-int clue_stage_times(clue_ctx *ctx, float *ms, int32_t cap, char *names, int64_t names_cap) {
-    if (!ctx || (cap > 0 && !ms)) return -CLUE_ERR_ARG;
-    if (!ctx->prof_recorded || ctx->prof_names.empty()) return -CLUE_ERR_STATE;
-    const int n = (int)ctx->prof_names.size();
+int clue_stage_times_back(clue_ctx *ctx, int32_t back, float *ms, int32_t cap, char *names,
+                          int64_t names_cap) {
+    if (!ctx || (cap > 0 && !ms) || back < 0) return -CLUE_ERR_ARG;
+    if (back >= ctx->prof_count) return -CLUE_ERR_STATE;
+    const int set = ((ctx->prof_set - 1 - back) % NPSETS + NPSETS) % NPSETS;
+    const auto &pn = ctx->prof_names[set];
+    if (pn.empty()) return -CLUE_ERR_STATE;
+    const int n = (int)pn.size();
     if (names && names_cap > 0) {
         std::string all;
         for (int i = 0; i < n; ++i) {
             if (i) all += ",";
-            all += ctx->prof_names[i];
+            all += pn[i];
         }
         std::strncpy(names, all.c_str(), (size_t)names_cap - 1);
         names[names_cap - 1] = 0;
     }
-    cudaError_t e = cudaEventSynchronize(ctx->pev[n]);
+    cudaError_t e = cudaEventSynchronize(ctx->pev[set][n]);
     if (e != cudaSuccess) return -cuda_fail(ctx, e, "cudaEventSynchronize");
     for (int i = 0; i < n && i < cap; ++i) {
-        e = cudaEventElapsedTime(&ms[i], ctx->pev[i], ctx->pev[i + 1]);
+        e = cudaEventElapsedTime(&ms[i], ctx->pev[set][i], ctx->pev[set][i + 1]);
         if (e != cudaSuccess) return -cuda_fail(ctx, e, "cudaEventElapsedTime");
     }
     return n;
+}
+
+int clue_stage_times(clue_ctx *ctx, float *ms, int32_t cap, char *names, int64_t names_cap) {
+    return clue_stage_times_back(ctx, 0, ms, cap, names, names_cap);
 }
 
 int32_t clue_last_launch_count(clue_ctx *ctx) { return ctx ? ctx->last_launches : 0; }

@@ -98,8 +98,8 @@ struct Buffers {
     int32_t *lay_s;      // [N] layer in sorted order
     // density
     float4 *spr;         // [N] sorted order: x, y, rho, id (written by the rho step)
-    float4 *hr;          // [N] by sorted position: rho, delta^2, nh (int bits: batch
-                         //     index or -1), read only by the intermediates export
+    float2 *hr;          // [N] by sorted position: delta^2, nh (int bits: batch index
+                         //     or -1), read only by the intermediates export
     // decision / expansion
     int32_t *code;       // [N] by hit: nh for a follower, else CODE_*; aliases key
     int32_t *fcount;     // [N] followers per hit (zeroed in the fill step)

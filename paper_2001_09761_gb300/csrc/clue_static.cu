@@ -139,7 +139,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.sp = (float4 *)take(NB * 16);
     b.lay_s = (int32_t *)take(NB * 4);
     b.rec = (float4 *)take(NB * 16);
-    b.hr = b.rec;
+    b.hr = (float2 *)b.rec;
     b.spr = (float4 *)take(NB * 16);
     b.code = b.key;
     b.fcount = (int32_t *)take(NB * 4);

@@ -281,11 +281,11 @@ __global__ void __launch_bounds__(256) k_export(Buffers b, float *rho, float *de
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
             const int g = __float_as_int(b.sp[q].w);
-            const float4 h = b.hr[q];
-            if (rho) rho[g] = h.x;
-            if (delta) delta[g] = sqrtf(h.y);
+            const float2 h = b.hr[q];
+            if (rho) rho[g] = b.spr[q].z;
+            if (delta) delta[g] = sqrtf(h.x);
             if (nh) {
-                const int j = __float_as_int(h.z);
+                const int j = __float_as_int(h.y);
                 nh[g] = j < 0 ? -1 : (int32_t)(j - hoff);
             }
         }

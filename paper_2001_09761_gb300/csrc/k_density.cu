@@ -240,8 +240,9 @@ cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cu
 // hits with d2 < d_m^2 and rho_j > rho_i (the minimum is order-free).  The
 // same thread takes the seed / outlier decision (Sec. 2.2), which needs only
 // this hit's rho, delta and nh, and stores one 4-byte code by hit (the
-// scattered store this step cannot avoid); rho, delta^2, nh also go, in
-// sorted order (coalesced), to a record the intermediates export reads.
+// scattered store this step cannot avoid); delta^2 and nh also go, in sorted
+// order (coalesced), to an 8-byte record the intermediates export reads (rho
+// stays in the rho step's sorted records).
 __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
     const float4 *__restrict__ sp = b.spr;  // x, y, rho, id
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
             const float d2v = found ? __uint_as_float((unsigned)(best >> 32))
                                     : __int_as_float(0x7f800000);  // +inf (Eq. 4)
             const int nhj = found ? (int)(unsigned)best : -1;
-            b.hr[q] = make_float4(ri, d2v, __int_as_float(nhj), 0.0f);
+            b.hr[q] = make_float2(d2v, __int_as_float(nhj));
             // the decision of Sec. 2.2 needs only this hit's rho, delta and nh:
             // seed, outlier, or a follower of nh (Algorithm 3), stored by hit
             const bool seed = (ri > p.rhoc) && (d2v > p.dcs2);

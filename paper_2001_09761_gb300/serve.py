@@ -48,6 +48,7 @@ class _Request:
     t_submit: float
     future: Future
     rid: int
+    keep: list = field(default_factory=list)   # host copies alive until staged
 
 
 @dataclass
@@ -97,14 +98,30 @@ class GpuBackend:
                 bf["hcid"], bf["hseed"] = pin(torch.int32), pin(torch.uint8)
 
     def stage(self, region: int, offset: int, req: _Request):
-        """Queue the copy of one event's inputs into a region."""
+        """Queue the copy of one event's inputs into a region (one library
+        call for the four arrays; host tensors or numpy arrays of the right
+        dtypes, pinned for asynchronous copies)."""
+        if req.n == 0:
+            return
         t = self.torch
         b = self.bufs[region]
-        with t.cuda.stream(self.copy_stream):
-            for key, arr, dt in (("x", req.x, t.float32), ("y", req.y, t.float32),
-                                 ("l", req.layer, t.int32), ("e", req.energy, t.float32)):
-                src = arr if isinstance(arr, t.Tensor) else t.from_numpy(np.ascontiguousarray(arr))
-                b[key][offset:offset + req.n].copy_(src.to(dt), non_blocking=True)
+        srcs = []
+        for arr, dt, tdt in ((req.x, np.float32, t.float32), (req.y, np.float32, t.float32),
+                             (req.layer, np.int32, t.int32),
+                             (req.energy, np.float32, t.float32)):
+            if isinstance(arr, t.Tensor):
+                a = arr.to(tdt).contiguous()
+                ptr = a.data_ptr()
+            else:
+                a = np.ascontiguousarray(arr, dtype=dt)
+                ptr = a.ctypes.data
+            req.keep.append(a)
+            srcs.append(ptr)
+        rc = self.clue.clue_stage_event(*srcs, req.n, b["x"].data_ptr(), b["y"].data_ptr(),
+                                        b["l"].data_ptr(), b["e"].data_ptr(), offset,
+                                        self.copy_stream.cuda_stream)
+        if rc:
+            raise self.clue.ClueError(rc, "clue_stage_event")
 
     def launch(self, region: int, offsets):
         """Cluster the region's events as one batch; returns a handle whose

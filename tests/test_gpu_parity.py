@@ -153,6 +153,37 @@ def test_repeated_runs_are_identical_and_graph_replay(clue_mod):
         assert np.array_equal(c, ref["cluster_id"]) and np.array_equal(s, ref["is_seed"])
 
 
+def test_profiled_graph_replay_keeps_each_runs_times(clue_mod):
+    """With profiling on, captured graphs stamp a ring of event sets, so the
+    times of the last 4 runs stay readable while later runs are queued, and
+    profiling changes no result."""
+    import torch
+    evs = [gen.make_event(n, 100, 60 + i, "blobs") for i, n in enumerate((30_000, 70_000))]
+    x, y, l, e, offs = gen.concat(evs)
+    d = lambda a: torch.from_numpy(a).cuda()
+    tx, ty, tl, te = d(x), d(y), d(l), d(e)
+    n = int(offs[-1])
+    cid = torch.empty(n, dtype=torch.int32, device="cuda")
+    seed = torch.empty(n, dtype=torch.uint8, device="cuda")
+    cl = _cl(clue_mod, gen.EXTENT, 100, use_graphs=True)
+    cl.set_profiling(True)
+    for r in range(7):  # direct, captured, then replays through all four sets
+        cl.run_batch(tx, ty, tl, te, offs, gen.PARAMS_BLOBS, out=(cid, seed))
+        if r >= 1:
+            prev = cl.kernel_times(back=1)  # read while run r is queued
+            assert {"fill_count", "rho", "nh_delta", "chase"} <= set(prev)
+    times = [cl.kernel_times(back=k) for k in range(4)]
+    for t in times:
+        assert set(t) == set(times[0]) and all(v >= 0 for v in t.values())
+    with pytest.raises(clue_mod.ClueError):
+        cl.kernel_times(back=4)
+    cl.sync()
+    c = cid.cpu().numpy()
+    for i, ev in enumerate(evs):
+        ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 100)
+        assert np.array_equal(c[offs[i]:offs[i + 1]], ref["cluster_id"])
+
+
 def test_host_pointer_path(clue_mod):
     evs = [gen.make_event(n, 100, 700 + i, "blobs") for i, n in enumerate([3000, 25000, 9000])]
     x, y, l, e, offs = gen.concat(evs)
