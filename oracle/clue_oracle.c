@@ -33,7 +33,11 @@
  *   R3  every comparison is strict, as printed: d < d_c, d < d_m, rho_j > rho_i,
  *       seed iff rho > rho_c and delta > delta_c, outlier iff rho < rho_c and
  *       delta > delta_o.
- *   R4  rho is summed in fp32, starting from +0, over N_dc(i) in ascending j.
+ *   R4  rho_i is the exact sum of the terms over N_dc(i) (w_j, or fl(chi(d_ij)
+ *       * w_j)), rounded once to the nearest fp32, ties to even.  Eq. 3 sums
+ *       over a set and fixes no order; the exact sum is the one fp32 value
+ *       that depends on the set alone (any fp32 addition order can differ
+ *       from it, and from another order, in the last bit).
  *   R5  among nearest-higher candidates at equal d2 the smallest j wins.
  *   R7  a hit that is neither seed nor outlier and has nh = -1 (possible only
  *       when rho == rho_c) is not registered anywhere and stays noise.
@@ -128,10 +132,94 @@ static float chi_value(int32_t kind, float inv, float d2)
     return 1.0f;
 }
 
-static int cmp_int64(const void *a, const void *b)
+/* Exact accumulation for R4.  A finite fp32 value is an integer multiple of
+ * 2^-149 below 2^128 in magnitude, i.e. an integer below 2^277 in units of
+ * 2^-149; a sum of up to 2^40 of them fits in a 320-bit two's-complement
+ * integer, kept here as ten 32-bit limbs, least significant first. */
+#define EXACT_LIMBS 10
+
+static void exact_add(uint32_t acc[EXACT_LIMBS], float t)
 {
-    int64_t p = *(const int64_t *)a, q = *(const int64_t *)b;
-    return (p > q) - (p < q);
+    uint32_t bits;
+    memcpy(&bits, &t, sizeof(bits));
+    const uint32_t e = (bits >> 23) & 0xffu;
+    const uint32_t frac = bits & 0x7fffffu;
+    /* |t| = mant * 2^(shift - 149): subnormals have e = 0, mant = frac */
+    const uint64_t mant = e ? (frac | 0x800000u) : frac;
+    const int shift = e ? (int)e - 1 : 0;
+    uint32_t add[EXACT_LIMBS] = {0};
+    const uint64_t v = mant << (shift % 32);       /* below 2^56: two limbs */
+    add[shift / 32] = (uint32_t)v;
+    add[shift / 32 + 1] = (uint32_t)(v >> 32);
+    if (bits >> 31) {                              /* negative: add -|t| */
+        uint64_t carry = 1;
+        for (int k = 0; k < EXACT_LIMBS; ++k) {
+            const uint64_t s = (uint64_t)(uint32_t)~add[k] + carry;
+            add[k] = (uint32_t)s;
+            carry = s >> 32;
+        }
+    }
+    uint64_t carry = 0;
+    for (int k = 0; k < EXACT_LIMBS; ++k) {
+        const uint64_t s = (uint64_t)acc[k] + add[k] + carry;
+        acc[k] = (uint32_t)s;
+        carry = s >> 32;
+    }
+}
+
+static int bit_at(const uint32_t m[EXACT_LIMBS], int i)
+{
+    return (int)((m[i / 32] >> (i % 32)) & 1u);
+}
+
+/* The accumulated value (units of 2^-149) rounded to the nearest fp32, ties
+ * to even, +0 for an exact zero, +-inf beyond the largest finite value. */
+static float exact_round(const uint32_t acc[EXACT_LIMBS])
+{
+    uint32_t mag[EXACT_LIMBS];
+    const uint32_t neg = acc[EXACT_LIMBS - 1] >> 31;
+    uint64_t carry = neg;
+    for (int k = 0; k < EXACT_LIMBS; ++k) {       /* |acc| by two's complement */
+        const uint64_t s = (uint64_t)(neg ? (uint32_t)~acc[k] : acc[k]) + carry;
+        mag[k] = (uint32_t)s;
+        carry = s >> 32;
+    }
+    int p = -1;                                    /* highest set bit */
+    for (int i = 32 * EXACT_LIMBS - 1; i >= 0; --i)
+        if (bit_at(mag, i)) {
+            p = i;
+            break;
+        }
+    if (p < 0)
+        return 0.0f;
+    uint32_t bits;
+    if (p <= 23) {
+        /* below 2^24 units: exactly a subnormal (or the smallest binade),
+         * whose bit pattern is the unit count itself */
+        bits = mag[0];
+    } else {
+        int sh = p - 23;                           /* keep bits [sh, p] */
+        uint32_t m = 0;
+        for (int b = 0; b < 24; ++b)
+            m |= (uint32_t)bit_at(mag, sh + b) << b;
+        const int guard = bit_at(mag, sh - 1);
+        int sticky = 0;
+        for (int b = 0; b < sh - 1; ++b)
+            sticky |= bit_at(mag, b);
+        if (guard && (sticky || (m & 1u))) {
+            m += 1;
+            if (m == (1u << 24)) {
+                m >>= 1;
+                sh += 1;
+            }
+        }
+        const int biased = sh + 1;                 /* value m * 2^(biased - 150) */
+        bits = biased >= 255 ? 0x7f800000u : ((uint32_t)biased << 23) | (m & 0x7fffffu);
+    }
+    bits |= neg << 31;
+    float f;
+    memcpy(&f, &bits, sizeof(f));
+    return f;
 }
 
 static int param_ok(float d)
@@ -193,7 +281,6 @@ int oracle_clue_chi(int64_t n, const float *x, const float *y, const int32_t *la
 
     int64_t *head = malloc(sizeof(int64_t) * (size_t)n_cells);
     int64_t *next = malloc(sizeof(int64_t) * (size_t)n);
-    int64_t *buf = malloc(sizeof(int64_t) * (size_t)n);
     float *rho = malloc(sizeof(float) * (size_t)n);
     float *d2v = malloc(sizeof(float) * (size_t)n);
     int64_t *nh = malloc(sizeof(int64_t) * (size_t)n);
@@ -203,9 +290,9 @@ int oracle_clue_chi(int64_t n, const float *x, const float *y, const int32_t *la
     int64_t *stack = malloc(sizeof(int64_t) * (size_t)n);
     uint8_t *seed = malloc((size_t)n);
     uint8_t *outl = malloc((size_t)n);
-    if (!head || !next || !buf || !rho || !d2v || !nh || !cid || !fol_head || !fol_next ||
+    if (!head || !next || !rho || !d2v || !nh || !cid || !fol_head || !fol_next ||
         !stack || !seed || !outl) {
-        free(head); free(next); free(buf); free(rho); free(d2v); free(nh); free(cid);
+        free(head); free(next); free(rho); free(d2v); free(nh); free(cid);
         free(fol_head); free(fol_next); free(stack); free(seed); free(outl);
         return ORACLE_ERR_OOM;
     }
@@ -221,33 +308,26 @@ int oracle_clue_chi(int64_t n, const float *x, const float *y, const int32_t *la
         head[c] = i;
     }
 
-    /* Step 2 (Eq. 3, Algorithm 1): rho_i over Omega_dc(i), summed in
-     * ascending j (R4). */
+    /* Step 2 (Eq. 3, Algorithm 1): rho_i over Omega_dc(i), the exact sum of
+     * its terms rounded once (R4). */
     for (int64_t i = 0; i < n; ++i) {
         double hx = window_half(dc, x[i]), hy = window_half(dc, y[i]);
         int64_t bx0 = axis_bin((double)x[i] - hx, x_min, s, nbx);
         int64_t bx1 = axis_bin((double)x[i] + hx, x_min, s, nbx);
         int64_t by0 = axis_bin((double)y[i] - hy, y_min, s, nby);
         int64_t by1 = axis_bin((double)y[i] + hy, y_min, s, nby);
-        int64_t m = 0;
+        uint32_t acc[EXACT_LIMBS] = {0};
         for (int64_t by = by0; by <= by1; ++by)
             for (int64_t bx = bx0; bx <= bx1; ++bx)
                 for (int64_t j = head[((int64_t)layer[i] * nby + by) * nbx + bx]; j >= 0;
-                     j = next[j])
-                    if (sq_dist(x[i], y[i], x[j], y[j]) < dc2)
-                        buf[m++] = j;
-        qsort(buf, (size_t)m, sizeof(int64_t), cmp_int64);
-        float r = 0.0f;
-        for (int64_t k = 0; k < m; ++k) {
-            const int64_t j = buf[k];
-            if (chi_kind == 0) {
-                r += w[j];
-            } else {
-                const float t = chi_value(chi_kind, chi_inv, sq_dist(x[i], y[i], x[j], y[j])) * w[j];
-                r += t;
-            }
-        }
-        rho[i] = r;
+                     j = next[j]) {
+                    const float d2 = sq_dist(x[i], y[i], x[j], y[j]);
+                    if (d2 < dc2) {
+                        const float t = chi_kind == 0 ? w[j] : chi_value(chi_kind, chi_inv, d2) * w[j];
+                        exact_add(acc, t);
+                    }
+                }
+        rho[i] = exact_round(acc);
     }
 
     /* Step 3 (Eq. 4, Algorithm 2): nearest-higher within d_m, ties by the
@@ -316,7 +396,7 @@ int oracle_clue_chi(int64_t n, const float *x, const float *y, const int32_t *la
     if (n_seeds_out)
         *n_seeds_out = k;
 
-    free(head); free(next); free(buf); free(rho); free(d2v); free(nh); free(cid);
+    free(head); free(next); free(rho); free(d2v); free(nh); free(cid);
     free(fol_head); free(fol_next); free(stack); free(seed); free(outl);
     return ORACLE_OK;
 }

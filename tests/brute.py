@@ -3,7 +3,8 @@
 A test-only pin for the oracle.  It follows the paper's definitions directly:
 N_d(i) is every hit of i's layer with d_ij < d (Eq. 2 with Omega = the whole
 layer, allowed since Omega only has to contain N), rho by Eq. 3 with the flat
-kernel summed in ascending j, nh/delta by Eq. 4 with the smaller index winning
+kernel as the exact rational sum rounded once to fp32 (reading R4),
+nh/delta by Eq. 4 with the smaller index winning
 a distance tie, the seed/outlier rule of Sec. 2.2, and cluster ids through the
 recursion "a follower inherits the id of its nearest-higher" (the closed form
 of passing ids down the follower chains) rather than a stack.
@@ -16,6 +17,8 @@ from __future__ import annotations
 import sys
 
 import numpy as np
+
+from exactsum import exact_rho
 
 
 def brute_clue(x, y, layer, w, params):
@@ -38,9 +41,7 @@ def brute_clue(x, y, layer, w, params):
         dy = yl[None, :] - yl[:, None]
         d2 = (dx * dx) + (dy * dy)                 # fp32, separately rounded
         near = d2 < dc2
-        r = np.zeros(idx.shape[0], np.float32)
-        for jj in range(idx.shape[0]):             # ascending j, fp32 adds
-            r = r + np.where(near[:, jj], wl[jj], np.float32(0.0)).astype(np.float32)
+        r = np.array([exact_rho(wl[near[i]]) for i in range(idx.shape[0])], np.float32)
         rho[idx] = r
         cand = (d2 < dm2) & (r[None, :] > r[:, None])
         masked = np.where(cand, d2, np.float32(np.inf))

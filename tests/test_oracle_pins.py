@@ -5,8 +5,8 @@
 * an O(n^2) brute force written from the definitions (no grid, recursive
   expansion instead of Algorithm 3's stack);
 * library routines: scipy's KD-tree for neighbour sets and nearest-higher
-  search, networkx for the follower forest, exact rational sums for rho's
-  rounding error;
+  search, networkx for the follower forest, exact rational sums (Python
+  fractions) for rho;
 * the paper's invariants (Sec. 2.2) and symmetries of the definitions.
 """
 from __future__ import annotations
@@ -20,6 +20,7 @@ import numpy as np
 import pytest
 
 from brute import brute_clue
+from exactsum import exact_rho
 from paper_2001_09761_gb300 import gen
 
 GOLDEN = Path(__file__).resolve().parent / "golden"
@@ -134,23 +135,58 @@ def test_invariants_on_generated_events(oracle_mod):
             assert cid[i] == (cid[j] if seed[j] else -1)
 
 
-def test_rho_within_rounding_bound_of_exact_sum(oracle_mod):
-    """The fp32 sum of m terms differs from the exact rational sum of the same
-    set by at most (m-1) u sum|w| (u = 2^-24; recursive summation bound).  This
-    pins the summed set N_dc(i) independently of the summation order."""
+def _adversarial_weights(rng, n):
+    """fp32 weights that make fp32 running sums order-dependent: magnitudes
+    from 1e-38 to 1e30, both signs, subnormals, zeros and exact cancellations."""
+    kind = rng.integers(0, 6, n)
+    w = np.where(kind == 0, rng.exponential(1.0, n),
+        np.where(kind == 1, 10.0 ** rng.uniform(-38, 30, n),
+        np.where(kind == 2, -rng.exponential(1.0, n),
+        np.where(kind == 3, rng.integers(1, 2 ** 20, n) * 2.0 ** -149,
+        np.where(kind == 4, 0.0, 1.0 + rng.integers(0, 8, n) * 2.0 ** -24)))))
+    return w.astype(np.float32)
+
+
+def test_rho_is_exact_sum_rounded_once(oracle_mod):
+    """Reading R4: rho_i is the exact rational sum of w_j over N_dc(i) rounded
+    once to fp32 (ties to even), checked hit by hit with Python's exact
+    fractions on weights chosen so that any fp32 running sum would differ."""
     ev = gen.make_event(600, 1, 3, "irregular", extent=(-15.0, 15.0, -15.0, 15.0))
+    w = _adversarial_weights(np.random.default_rng(7), ev.n)
     dc = np.float32(2.0)
-    o = oracle_mod.run_event(ev, gen.PARAMS_IRREGULAR, 1, extent=(-15.0, 15.0, -15.0, 15.0))
-    x, y, w = ev.x, ev.y, ev.energy
+    o = oracle_mod.run(ev.x, ev.y, ev.layer, w, gen.PARAMS_IRREGULAR, 1,
+                       (-15.0, 15.0, -15.0, 15.0))
+    x, y = ev.x, ev.y
     dx = x[None, :] - x[:, None]
     dy = y[None, :] - y[:, None]
     near = (dx * dx + dy * dy) < dc * dc
-    u = Fraction(1, 2 ** 24)
     for i in range(ev.n):
-        js = np.nonzero(near[i])[0]
-        exact = sum((Fraction(float(w[j])) for j in js), Fraction(0))
-        bound = (len(js) - 1) * u * sum((Fraction(abs(float(w[j]))) for j in js), Fraction(0))
-        assert abs(Fraction(float(o["rho"][i])) - exact) <= bound
+        want = exact_rho(w[near[i]])
+        assert o["rho"][i].view(np.uint32) == want.view(np.uint32), (i, o["rho"][i], want)
+
+
+def test_rho_exact_sum_of_coincident_hits(oracle_mod):
+    """All hits of a layer at one point are mutual neighbours, so every rho
+    is the rounded exact sum of the whole layer: the summation alone, on
+    sets built to round up, down, to even, to a subnormal, to zero by
+    cancellation, to infinity and up across a power of two."""
+    rng = np.random.default_rng(11)
+    sets = [_adversarial_weights(rng, int(rng.integers(1, 60))) for _ in range(120)]
+    sets += [np.array([1.0, 2.0 ** -24, 2.0 ** -25], np.float32),             # up (not a tie)
+             np.array([1.0, 2.0 ** -24], np.float32),                          # tie, to even
+             np.array([1.0 + 2.0 ** -23, 2.0 ** -24], np.float32),             # tie, to even (up)
+             np.array([2.0 ** -149] * 5, np.float32),                          # subnormal
+             np.array([3.0e38, 3.0e38, -1.0], np.float32),                     # overflow
+             np.array([1e30, -1e30, 2.0 ** -140], np.float32),                 # cancellation
+             np.array([5.0, -5.0], np.float32),                                # exact zero
+             np.array([1.0, 1.0 - 2.0 ** -24, 2.0 ** -25], np.float32)]        # up into 2.0
+    for w in sets:
+        n = w.size
+        z = np.zeros(n, np.float32)
+        o = oracle_mod.run(z, z, np.zeros(n, np.int32), w, (1.0, 0.0, 1.0, 1.0), 1,
+                           (-1.0, 1.0, -1.0, 1.0))
+        want = exact_rho(w)
+        assert np.all(o["rho"].view(np.uint32) == want.view(np.uint32)), (w, o["rho"][0], want)
 
 
 def test_neighbour_sets_match_kdtree(oracle_mod):
@@ -235,15 +271,19 @@ def _partition(cid):
     return sorted(tuple(v) for v in groups.values())
 
 
-def test_permutation_invariance_unit_weights(oracle_mod):
-    """With unit weights rho is an exact integer, so relabelling the hits can
-    only change cluster ids, not the partition, barring distance ties."""
+@pytest.mark.parametrize("kind", ["paper", "blobs"])
+def test_permutation_invariance(oracle_mod, kind):
+    """rho is a function of the neighbour set alone (R4), so relabelling the
+    hits permutes rho bit for bit and can only change cluster ids, not the
+    partition, barring distance ties (unit weights for "paper", real-valued
+    energies for "blobs")."""
     ext = (-40.0, 40.0, -40.0, 40.0)
-    ev = gen.make_event(3000, 2, 17, "paper", extent=ext)
-    a = oracle_mod.run_event(ev, gen.PARAMS_PAPER, 2, extent=ext)
+    ev = gen.make_event(3000, 2, 17, kind, extent=ext)
+    params = gen.PARAMS_PAPER if kind == "paper" else gen.PARAMS_BLOBS
+    a = oracle_mod.run_event(ev, params, 2, extent=ext)
     perm = np.random.default_rng(1).permutation(ev.n)
     b = oracle_mod.run(ev.x[perm], ev.y[perm], ev.layer[perm], ev.energy[perm],
-                       gen.PARAMS_PAPER, 2, extent=ext)
+                       params, 2, extent=ext)
     inv = np.argsort(perm)
     assert np.array_equal(b["rho"][inv], a["rho"])
     back = b["cluster_id"][inv]
@@ -367,6 +407,16 @@ def test_chi_rho_within_bound_of_exact(oracle_mod, chi, s):
     u = 2.0 ** -24
     bound = (24 * u + (m - 1) * u) * np.abs(t).sum(1) + 1e-37
     assert np.all(np.abs(o["rho"].astype(np.float64) - exact) <= bound)
+    # R4: the exact sum of the fp32 terms fl(chi * w), chi from the oracle's
+    # own exp (pinned above), rounded once
+    inv = np.float32(1.0) / (np.float32(2.0) * np.float32(s) * np.float32(s)) if chi == 1 \
+        else np.float32(1.0) / np.float32(s)
+    for i in range(0, ev.n, 7):
+        js = np.nonzero(near[i])[0]
+        arg = (d2[i, js] * inv) if chi == 1 else (np.sqrt(d2[i, js]) * inv)
+        terms = np.array([np.float32(oracle_mod.chi_exp(-float(a))) for a in arg.astype(np.float32)],
+                         np.float32) * w[js]
+        assert o["rho"][i].view(np.uint32) == exact_rho(terms).view(np.uint32)
     # and the flat kernel is the special case chi = 1
     flat = oracle_mod.run_event(ev, (dc, 3.0, 2.0, 4.0), 1, extent=ext)
     big = oracle_mod.run_event(ev, (dc, 3.0, 2.0, 4.0), 1, extent=ext, chi=0, chi_param=0.0)
