@@ -7,15 +7,16 @@
 // the sorted array, so a window row is one contiguous run.  Each sorted hit is
 // one float4 (x, y, w, id), so a candidate costs one 16-byte load.
 //
-// rho is summed in fp32 in ascending hit index j over N_dc(i) of chi(d_ij) w_j
-// (flat chi = 1 unless the context asks for the Gaussian or exponential kernel
-// that Eq. 3 names; chi is computed by chi_exp, bit-reproducible) (the order is
-// part of the result's definition, independent of the bin size): every cell
-// lists its hits in ascending index, and the kernel merges the lists of the
-// window's non-empty cells, adding w_j for each j that passes the distance
-// test as the merge reaches it.  With the bin at least 2 R wide a window has
-// at most 2 x 2 cells, merged by one loop that every lane of a warp runs
-// alike (lanes that take different code paths would run one after another).
+// rho_i is the exact sum over N_dc(i) of the terms chi(d_ij) w_j (flat chi =
+// 1 unless the context asks for the Gaussian or exponential kernel that Eq. 3
+// names; chi is computed by chi_exp, bit-reproducible), rounded once to the
+// nearest fp32: a function of the neighbour set alone, so the window is read
+// in any order.  The kernel adds the terms with an error-free transformation
+// (TwoSum: s + t = s' + e exactly) into a running sum s and an error sum c,
+// and proves c exact from the smallest term and the largest |s| (below);
+// then s + c is the exact sum and one fp32 addition rounds it correctly.
+// When the proof fails (terms over more than ~24 binary orders of magnitude,
+// or an overflow) an integer accumulator recomputes the sum exactly.
 #include <climits>
 
 #include "device_common.cuh"
@@ -38,187 +39,153 @@ __device__ __forceinline__ Window window_of(float xi, float yi, float dr, const 
 
 __device__ __forceinline__ int id_of(const float4 &h) { return __float_as_int(h.w); }
 
-// r + chi(d) w for a candidate within d_c (flat: r + w exactly).
-template <int CHI = 0>
-__device__ __forceinline__ float add_if_near(float r, float xi, float yi, const float4 &h,
-                                             float dc2, float inv = 1.0f) {
-    const float d2 = sq_dist(xi, yi, h.x, h.y);
-    if (CHI == 0) return d2 < dc2 ? __fadd_rn(r, h.z) : r;
-    return d2 < dc2 ? __fadd_rn(r, __fmul_rn(chi_of<CHI>(d2, inv), h.z)) : r;
-}
+// ---- exact sum of fp32 values -------------------------------------------
+//
+// A finite fp32 value is an integer multiple of 2^-149 below 2^128, i.e. an
+// integer below 2^277 in units of 2^-149; Wide holds such sums exactly as a
+// 320-bit two's-complement integer (five 64-bit words, low word first).
+struct Wide {
+    unsigned long long v[5];
+};
 
-// Merge of up to K sorted cell lists given as [p[k], e[k]) (k < nk).  With
-// CACHE the head hit of every list stays in registers (one load per
-// candidate); without it only the head ids do (fewer registers, two loads).
-template <int K, bool CACHE, int CHI>
-__device__ __forceinline__ float merge_k(const float4 *__restrict__ sp, int (&p)[K],
-                                         const int (&e)[K], int nk, float xi, float yi,
-                                         float dc2, float inv) {
-    float4 h[CACHE ? K : 1];
-    int head[K];
+__device__ __forceinline__ void wide_add(Wide &a, float t) {
+    const unsigned bits = __float_as_uint(t);
+    const unsigned ex = (bits >> 23) & 0xffu;
+    const unsigned long long mant = ex ? ((bits & 0x7fffffu) | 0x800000u) : (bits & 0x7fffffu);
+    const int shift = ex ? (int)ex - 1 : 0;  // |t| = mant 2^(shift - 149)
+    const int k = shift >> 6, o = shift & 63;
+    const unsigned long long lo = mant << o;
+    const unsigned long long hi = o ? mant >> (64 - o) : 0ull;
+    const bool neg = bits >> 31;
+    unsigned long long carry = 0ull;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const bool live = k < nk && p[k] < e[k];
-        const float4 v = live ? sp[p[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (CACHE) h[k] = v;
-        head[k] = live ? id_of(v) : INT_MAX;
-    }
-    float r = 0.0f;
-    while (true) {
-        int m = head[0], am = 0;
-#pragma unroll
-        for (int k = 1; k < K; ++k)
-            if (head[k] < m) {
-                m = head[k];
-                am = k;
-            }
-        if (m == INT_MAX) break;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-            if (am == k) {
-                const int q = p[k]++;
-                r = add_if_near<CHI>(r, xi, yi, CACHE ? h[k] : sp[q], dc2, inv);
-                const bool live = q + 1 < e[k];
-                if (CACHE) {
-                    h[k] = live ? sp[q + 1] : h[k];
-                    head[k] = live ? id_of(h[k]) : INT_MAX;
-                } else {
-                    head[k] = live ? id_of(sp[q + 1]) : INT_MAX;
-                }
-            }
-    }
-    return r;
-}
-
-// Windows of at most 3 x 3 cells (a bin size between d_c and 2 d_c).
-template <int CHI>
-__device__ __forceinline__ float rho_window9(const Buffers &b, int64_t plane, int nbx, const Window &w, float xi,
-                             float yi, float dc2, float inv) {
-    int p[9], e[9];
-    int nk = 0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        p[k] = e[k] = 0;
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int cx = k % 3, cy = k / 3;
-        int a = 0, z = 0;
-        if ((w.lx + cx <= w.hx) && (w.ly + cy <= w.hy)) {
-            const int64_t c = plane + (int64_t)(w.ly + cy) * nbx + (w.lx + cx);
-            a = b.cell_start[c];
-            z = b.cell_start[c + 1];
+    for (int i = 0; i < 5; ++i) {
+        const unsigned long long d = i == k ? lo : (i == k + 1 ? hi : 0ull);
+        const unsigned long long x = a.v[i];
+        if (!neg) {
+            const unsigned long long s1 = x + d, s2 = s1 + carry;
+            carry = (s1 < x) | (s2 < s1);
+            a.v[i] = s2;
+        } else {
+            const unsigned long long d1 = x - d, d2 = d1 - carry;
+            carry = (x < d) | (d1 < carry);
+            a.v[i] = d2;
         }
-        const bool ne = a < z;
+    }
+}
+
+// The Wide value rounded to the nearest fp32, ties to the even significand.
+__device__ float wide_round(const Wide &a) {
+    const bool neg = a.v[4] >> 63;
+    unsigned long long m[5];
+    unsigned long long carry = neg ? 1ull : 0ull;  // |a| = ~a + 1 when negative
 #pragma unroll
-        for (int m = 0; m < 9; ++m)
-            if (ne && m == nk) {
-                p[m] = a;
-                e[m] = z;
-            }
-        nk += ne;
+    for (int i = 0; i < 5; ++i) {
+        const unsigned long long x = neg ? ~a.v[i] : a.v[i];
+        m[i] = x + carry;
+        carry = (m[i] < x) ? 1ull : 0ull;
     }
-    return merge_k<9, false, CHI>(b.sp, p, e, nk, xi, yi, dc2, inv);
+    int top = -1;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        if (m[i]) top = 64 * i + 63 - __clzll((long long)m[i]);
+    unsigned bits;
+    if (top < 0) {
+        bits = 0u;
+    } else if (top < 24) {
+        bits = (unsigned)m[0];  // a subnormal or the lowest binade: the unit count
+    } else {
+        int sh = top - 23;  // the kept significand is bits [sh, top]
+        auto bit = [&](int i) -> unsigned { return (unsigned)(m[i >> 6] >> (i & 63)) & 1u; };
+        unsigned sig = 0u;
+        for (int i = 0; i < 24; ++i) sig |= bit(sh + i) << i;
+        const unsigned guard = bit(sh - 1);
+        bool sticky = false;
+        for (int i = 0; i < sh - 1; ++i) sticky = sticky || bit(i);
+        if (guard && (sticky || (sig & 1u))) {
+            if (++sig == (1u << 24)) {
+                sig >>= 1;
+                ++sh;
+            }
+        }
+        bits = sh + 1 >= 255 ? 0x7f800000u : ((unsigned)(sh + 1) << 23) | (sig & 0x7fffffu);
+    }
+    return __uint_as_float(bits | (neg ? 0x80000000u : 0u));
 }
 
-// Any window size: repeatedly take the smallest id above the last one taken.
-// Quadratic in the window population; used only when the window spans more
-// than 3 x 3 bins (a bin size near d_c plus rounding at a bin edge).
+// chi(d) w of a neighbour at squared distance d2 (flat: w).
 template <int CHI>
-__device__ __forceinline__ float rho_select(const Buffers &b, int64_t plane, int nbx, const Window &w, float xi,
-                            float yi, float dc2, float inv) {
-    float r = 0.0f;
-    int last = -1;
-    while (true) {
-        int best = INT_MAX, bq = -1;
-        for (int by = w.ly; by <= w.hy; ++by)
-            for (int bx = w.lx; bx <= w.hx; ++bx) {
-                const int64_t c = plane + (int64_t)by * nbx + bx;
-                const int e = b.cell_start[c + 1];
-                for (int q = b.cell_start[c]; q < e; ++q) {
-                    const int j = id_of(b.sp[q]);
-                    if (j > last) {  // cells are ascending: the first one above `last`
-                        if (j < best) {
-                            best = j;
-                            bq = q;
-                        }
-                        break;
-                    }
-                }
-            }
-        if (bq < 0) break;
-        r = add_if_near<CHI>(r, xi, yi, b.sp[bq], dc2, inv);
-        last = best;
-    }
-    return r;
+__device__ __forceinline__ float term_of(float d2, float w, float inv) {
+    if (CHI == 0) return w;
+    return __fmul_rn(chi_of<CHI>(d2, inv), w);
 }
 
-// Windows of at most 2 x 2 cells.  Every lane runs the same loop (a lane
-// whose window has fewer cells just has empty cursors), so lanes of a warp
-// never take different code paths; a cursor keeps only its head id in a
-// register and the chosen candidate is loaded once.
+// rho by the integer accumulator: the rare windows the fast path cannot prove.
 template <int CHI>
-__device__ __forceinline__ float rho_window4(const Buffers &b, int64_t plane, int nbx,
-                                             const Window &w, float xi, float yi, float dc2,
-                                             float inv) {
+__device__ __noinline__ float rho_wide(const Buffers &b, int64_t plane, int nbx, Window w,
+                                       float xi, float yi, float dc2, float inv) {
+    Wide acc{{0ull, 0ull, 0ull, 0ull, 0ull}};
+    for (int by = w.ly; by <= w.hy; ++by) {
+        const int64_t row = plane + (int64_t)by * nbx;
+        const int e = b.cell_start[row + w.hx + 1];
+        for (int u = b.cell_start[row + w.lx]; u < e; ++u) {
+            const float4 h = b.sp[u];
+            const float d2 = sq_dist(xi, yi, h.x, h.y);
+            if (d2 < dc2) wide_add(acc, term_of<CHI>(d2, h.z, inv));
+        }
+    }
+    return wide_round(acc);
+}
+
+// Why the fast path is exact.  Let every nonzero term be a multiple of
+// 2^(g - 150) (g = the biased exponent of the smallest nonzero |term|, at
+// least 1).  Then every running sum s_k and every TwoSum error e_k is one too,
+// and |e_k| <= ulp(s_k) / 2 <= 2^(E - 151), E the biased exponent of
+// max |s_k|.  With m < 2^L terms the exact error sum, and each partial one,
+// is a multiple of 2^(g - 150) below 2^(L + E - 151) <= 2^(g - 126) when
+// L + E - 25 <= g: at most 24 significant bits, so an fp32 value, and
+// c = fl(c + e_k) never rounds.  Then s + c is the exact sum.
+template <int CHI>
+__global__ void __launch_bounds__(256) k_rho(Buffers b, Params p) {
     const float4 *__restrict__ sp = b.sp;
-    const int4 *__restrict__ spi = reinterpret_cast<const int4 *>(b.sp);  // id = .w
-    int p0, p1, p2, p3, e0, e1, e2, e3;
-    {
-        const int64_t r0 = plane + (int64_t)w.ly * nbx + w.lx;
-        const bool two_x = w.hx > w.lx, two_y = w.hy > w.ly;
-        p0 = b.cell_start[r0];
-        e0 = b.cell_start[r0 + 1];
-        p1 = e0;
-        e1 = two_x ? b.cell_start[r0 + 2] : e0;
-        const int64_t r1 = r0 + nbx;
-        p2 = two_y ? b.cell_start[r1] : 0;
-        e2 = two_y ? b.cell_start[r1 + 1] : 0;
-        p3 = e2;
-        e3 = (two_x && two_y) ? b.cell_start[r1 + 2] : e2;
-    }
-    int h0 = p0 < e0 ? spi[p0].w : INT_MAX;
-    int h1 = p1 < e1 ? spi[p1].w : INT_MAX;
-    int h2 = p2 < e2 ? spi[p2].w : INT_MAX;
-    int h3 = p3 < e3 ? spi[p3].w : INT_MAX;
-    float r = 0.0f;
-    while (true) {
-        const int m = min(min(h0, h1), min(h2, h3));
-        if (m == INT_MAX) break;
-        int q, e;
-        if (m == h0) { q = p0++; e = e0; }
-        else if (m == h1) { q = p1++; e = e1; }
-        else if (m == h2) { q = p2++; e = e2; }
-        else { q = p3++; e = e3; }
-        r = add_if_near<CHI>(r, xi, yi, sp[q], dc2, inv);
-        const int nx = q + 1 < e ? spi[q + 1].w : INT_MAX;
-        if (m == h0) h0 = nx;
-        else if (m == h1) h1 = nx;
-        else if (m == h2) h2 = nx;
-        else h3 = nx;
-    }
-    return r;
-}
-
-template <int CHI>
-__global__ void __launch_bounds__(256, 1) k_rho(Buffers b, Params p) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const EventDesc ev = b.events[tl.event];
         const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
-            const float4 me = b.sp[q];
+            const float4 me = sp[q];
             const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
             const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
-            const int nx = w.hx - w.lx + 1, ny = w.hy - w.ly + 1;
-            float r;
-            if (nx <= 2 && ny <= 2)
-                r = rho_window4<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv);
-            else if (nx <= 3 && ny <= 3)
-                r = rho_window9<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv);
-            else
-                r = rho_select<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv);
+            float s = 0.0f, c = 0.0f, smax = 0.0f;
+            unsigned tmin = 0x7f800000u;  // bits of the smallest nonzero |term|
+            int m = 0;
+            for (int by = w.ly; by <= w.hy; ++by) {
+                const int64_t row = plane + (int64_t)by * ev.nbx;
+                const int e = b.cell_start[row + w.hx + 1];
+                for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
+                    const float4 h = sp[u];
+                    const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                    const bool near = d2 < p.dc2;
+                    const float tv = near ? term_of<CHI>(d2, h.z, p.chi_inv) : 0.0f;
+                    // TwoSum: s + tv = s1 + err exactly
+                    const float s1 = __fadd_rn(s, tv);
+                    const float bb = __fsub_rn(s1, s);
+                    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(tv, bb));
+                    s = s1;
+                    c = __fadd_rn(c, err);
+                    smax = fmaxf(smax, fabsf(s1));
+                    const unsigned ta = __float_as_uint(tv) & 0x7fffffffu;
+                    tmin = ta ? min(tmin, ta) : tmin;
+                    m += near;
+                }
+            }
+            const int g = max((int)(tmin >> 23), 1);             // 2^(g - 150): last place
+            const int E = max((int)(__float_as_uint(smax) >> 23), 1);
+            const int L = 32 - __clz(m);
+            const bool exact = E < 255 && L + E - 25 <= g;
+            const float r = exact ? __fadd_rn(s, c)
+                                  : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv);
             b.spr[q] = make_float4(me.x, me.y, r, me.w);  // x, y, rho, id for the nh step
         }
     }

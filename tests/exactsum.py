@@ -43,3 +43,15 @@ def exact_rho(terms) -> np.float32:
     """The exact sum of the fp32 terms, rounded once (R4)."""
     return round_to_f32(sum((Fraction(float(t)) for t in np.asarray(terms, np.float32)),
                             Fraction(0)))
+
+
+def adversarial_weights(rng, n):
+    """fp32 weights that make fp32 running sums order-dependent: magnitudes
+    from 1e-38 to 1e30, both signs, subnormals, zeros and exact cancellations."""
+    kind = rng.integers(0, 6, n)
+    w = np.where(kind == 0, rng.exponential(1.0, n),
+        np.where(kind == 1, 10.0 ** rng.uniform(-38, 30, n),
+        np.where(kind == 2, -rng.exponential(1.0, n),
+        np.where(kind == 3, rng.integers(1, 2 ** 20, n) * 2.0 ** -149,
+        np.where(kind == 4, 0.0, 1.0 + rng.integers(0, 8, n) * 2.0 ** -24)))))
+    return w.astype(np.float32)

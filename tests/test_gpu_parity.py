@@ -184,6 +184,39 @@ def test_profiled_graph_replay_keeps_each_runs_times(clue_mod):
         assert np.array_equal(c[offs[i]:offs[i + 1]], ref["cluster_id"])
 
 
+def test_exact_rho_with_adversarial_weights(clue_mod):
+    """Reading R4 on the GPU: weights over 1e-38..1e30, both signs,
+    subnormals and zeros, so many windows fail the fast path's exactness
+    proof and take the integer accumulator; every output is bit-exact."""
+    from exactsum import adversarial_weights
+    ev = gen.make_event(30_000, 5, 77, "blobs")
+    w = adversarial_weights(np.random.default_rng(5), ev.n)
+    cl = _cl(clue_mod, gen.EXTENT, 5)
+    ev2 = gen.Event(ev.x, ev.y, ev.layer, w)
+    assert_parity(_gpu_all(cl, ev2, gen.PARAMS_BLOBS),
+                  oracle.run(ev.x, ev.y, ev.layer, w, gen.PARAMS_BLOBS, 5))
+
+
+def test_exact_rho_of_coincident_sets(clue_mod):
+    """Hits at one point are mutual neighbours, so rho is the rounded exact
+    sum of the whole set: rounding up, to even, to a subnormal, to zero by
+    cancellation, to infinity and across a power of two, against the oracle."""
+    from exactsum import adversarial_weights
+    rng = np.random.default_rng(11)
+    sets = [adversarial_weights(rng, int(rng.integers(1, 60))) for _ in range(40)]
+    sets += [np.array(v, np.float32) for v in (
+        [1.0, 2.0 ** -24, 2.0 ** -25], [1.0, 2.0 ** -24], [1.0 + 2.0 ** -23, 2.0 ** -24],
+        [2.0 ** -149] * 5, [3.0e38, 3.0e38, -1.0], [1e30, -1e30, 2.0 ** -140], [5.0, -5.0],
+        [1.0, 1.0 - 2.0 ** -24, 2.0 ** -25])]
+    cl = _cl(clue_mod, (-1.0, 1.0, -1.0, 1.0), 1)
+    for w in sets:
+        z = np.zeros(w.size, np.float32)
+        ev = gen.Event(z, z, np.zeros(w.size, np.int32), w)
+        g = _gpu_all(cl, ev, (1.0, 0.0, 1.0, 1.0))
+        ref = oracle.run(z, z, ev.layer, w, (1.0, 0.0, 1.0, 1.0), 1, (-1.0, 1.0, -1.0, 1.0))
+        assert_parity(g, ref)
+
+
 def test_host_pointer_path(clue_mod):
     evs = [gen.make_event(n, 100, 700 + i, "blobs") for i, n in enumerate([3000, 25000, 9000])]
     x, y, l, e, offs = gen.concat(evs)

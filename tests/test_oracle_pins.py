@@ -20,7 +20,7 @@ import numpy as np
 import pytest
 
 from brute import brute_clue
-from exactsum import exact_rho
+from exactsum import adversarial_weights, exact_rho
 from paper_2001_09761_gb300 import gen
 
 GOLDEN = Path(__file__).resolve().parent / "golden"
@@ -135,24 +135,12 @@ def test_invariants_on_generated_events(oracle_mod):
             assert cid[i] == (cid[j] if seed[j] else -1)
 
 
-def _adversarial_weights(rng, n):
-    """fp32 weights that make fp32 running sums order-dependent: magnitudes
-    from 1e-38 to 1e30, both signs, subnormals, zeros and exact cancellations."""
-    kind = rng.integers(0, 6, n)
-    w = np.where(kind == 0, rng.exponential(1.0, n),
-        np.where(kind == 1, 10.0 ** rng.uniform(-38, 30, n),
-        np.where(kind == 2, -rng.exponential(1.0, n),
-        np.where(kind == 3, rng.integers(1, 2 ** 20, n) * 2.0 ** -149,
-        np.where(kind == 4, 0.0, 1.0 + rng.integers(0, 8, n) * 2.0 ** -24)))))
-    return w.astype(np.float32)
-
-
 def test_rho_is_exact_sum_rounded_once(oracle_mod):
     """Reading R4: rho_i is the exact rational sum of w_j over N_dc(i) rounded
     once to fp32 (ties to even), checked hit by hit with Python's exact
     fractions on weights chosen so that any fp32 running sum would differ."""
     ev = gen.make_event(600, 1, 3, "irregular", extent=(-15.0, 15.0, -15.0, 15.0))
-    w = _adversarial_weights(np.random.default_rng(7), ev.n)
+    w = adversarial_weights(np.random.default_rng(7), ev.n)
     dc = np.float32(2.0)
     o = oracle_mod.run(ev.x, ev.y, ev.layer, w, gen.PARAMS_IRREGULAR, 1,
                        (-15.0, 15.0, -15.0, 15.0))
@@ -171,7 +159,7 @@ def test_rho_exact_sum_of_coincident_hits(oracle_mod):
     sets built to round up, down, to even, to a subnormal, to zero by
     cancellation, to infinity and up across a power of two."""
     rng = np.random.default_rng(11)
-    sets = [_adversarial_weights(rng, int(rng.integers(1, 60))) for _ in range(120)]
+    sets = [adversarial_weights(rng, int(rng.integers(1, 60))) for _ in range(120)]
     sets += [np.array([1.0, 2.0 ** -24, 2.0 ** -25], np.float32),             # up (not a tie)
              np.array([1.0, 2.0 ** -24], np.float32),                          # tie, to even
              np.array([1.0 + 2.0 ** -23, 2.0 ** -24], np.float32),             # tie, to even (up)
