@@ -173,7 +173,7 @@ def run_reference(args):
 ALG_BYTES = {
     "fill_count": 16 + 4 + 4 + 4,      # x, y, w, layer in; cell, rank, cell count out
     "fill_scatter": 4 + 4 + 4 + 4,     # cell, rank, cell start in; hit id out
-    "fill_canon": 4 + 16 + 8 + 16 + 4,  # id, packed record, cell range in; sorted hit, layer out
+    "fill_canon": 4 + 16 + 16 + 4,     # id, packed record in; sorted hit, layer out
     "rho": 16 + 4 + 4,                 # x, y, w, id, layer in; rho out
     "nh_delta": 16 + 4 + 4 + 8,        # x, y, rho, id, layer in; code, (delta^2, nh) out
     "link": 4 + 4 + 4 + 1,             # code, seed rank in; id, seed flag out

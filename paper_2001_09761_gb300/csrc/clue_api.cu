@@ -225,7 +225,6 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     b.cell_start = (int32_t *)take((c + 1) * 4);
     b.perm = (int32_t *)take(n * 4);
     b.tmp = (int32_t *)take(n * 4);
-    b.big = (int32_t *)take((n / SMALL_SEGMENT + 1) * 4);
     b.sp = (float4 *)take(n * 16);
     b.lay_s = (int32_t *)take(n * 4);
     // one 16-byte-per-hit region: the grid fill's slot records, then (after
@@ -365,9 +364,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(rec("fill_scatter"));
     CK(launch_fill_canon(b, cfg, s));
     CK(rec("fill_canon"));
-    CK(launch_fill_big(b, cfg, s));
-    CK(rec("fill_big"));
-    nl += 4;
+    nl += 3;
     CK(launch_rho(b, p, cfg, s));
     CK(rec("rho"));
     CK(launch_nh(b, p, cfg, s));

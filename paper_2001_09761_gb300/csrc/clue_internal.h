@@ -12,7 +12,6 @@ constexpr int TILE = 1024;
 
 // A cell segment longer than this is sorted by one CTA (radix) instead of by
 // per-slot ranking.
-constexpr int SMALL_SEGMENT = 128;
 
 // cluster id of a follower whose id has not been passed down yet.
 constexpr int32_t PENDING = -2;
@@ -51,7 +50,6 @@ constexpr int EXPAND_LEVELS = 12;
 struct Ctrl {
     unsigned err;        // ERRBIT_* raised by any kernel
     unsigned overflow;   // the expansion left nodes for the completion pass
-    int32_t nbig;        // cell segments queued for the CTA sorter
     int32_t fsize[3];    // frontier sizes, rotating over the expansion levels
 };
 
@@ -92,8 +90,7 @@ struct Buffers {
     float4 *rec;         // [N] by hit: x, y, w, local cell (int bits), for the
                          //     ranking's gather; aliases hr
     int32_t *perm;       // [N] hit ids grouped by cell, unordered within a cell
-    int32_t *tmp;        // [N] scratch for the CTA sorter
-    int32_t *big;        // [N / SMALL_SEGMENT + 1] cells queued for the CTA sorter
+    int32_t *tmp;        // [N] the second expansion frontier
     float4 *sp;          // [N] hits sorted by (cell, id): x, y, w, id (int bits)
     int32_t *lay_s;      // [N] layer in sorted order
     // density
@@ -128,7 +125,6 @@ cudaError_t launch_fill_count(const Buffers &b, const Params &p, const LaunchCfg
 cudaError_t launch_scan_cells(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
 cudaError_t launch_fill_scatter(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_fill_big(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s,

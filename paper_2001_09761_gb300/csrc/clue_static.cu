@@ -37,7 +37,7 @@ constexpr size_t NB = (size_t)STATIC_MAX_HITS, CB = (size_t)STATIC_MAX_CELLS;
 constexpr size_t STATIC_BYTES =
     al(sizeof(Ctrl)) + al(sizeof(EventDesc)) + al(STATIC_MAX_TILES * sizeof(Tile)) +
     al(NB * 4) /*key*/ + al(NB * 4) /*rank*/ + al(CB * 4) /*count*/ + al((CB + 1) * 4) /*cell_start*/ +
-    al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ + al((NB / SMALL_SEGMENT + 1) * 4) /*big*/ +
+    al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ +
     al(NB * 16) /*sp*/ + al(NB * 4) /*lay_s*/ +
     al(NB * 16) /*rec = hr*/ + al(NB * 16) /*spr*/ +
     al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
@@ -135,7 +135,6 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.cell_start = (int32_t *)take((CB + 1) * 4);
     b.perm = (int32_t *)take(NB * 4);
     b.tmp = (int32_t *)take(NB * 4);
-    b.big = (int32_t *)take((NB / SMALL_SEGMENT + 1) * 4);
     b.sp = (float4 *)take(NB * 16);
     b.lay_s = (int32_t *)take(NB * 4);
     b.rec = (float4 *)take(NB * 16);
@@ -223,7 +222,6 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     SCK(launch_scan_cells(b, cfg, s, &nl));
     SCK(launch_fill_scatter(b, cfg, s));
     SCK(launch_fill_canon(b, cfg, s));
-    SCK(launch_fill_big(b, cfg, s));
     SCK(launch_rho(b, prm, cfg, s));
     SCK(launch_nh(b, prm, cfg, s));
     SCK(launch_scan_hits(b, prm, cfg, s, &nl));

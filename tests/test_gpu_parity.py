@@ -375,7 +375,7 @@ def test_stage_times_and_launch_count(clue_mod):
         assert all(v >= 0 for v in st.values())
         kt = cl.kernel_times()
         assert {"fill_count", "rho", "nh_delta"} | last <= set(kt)
-        assert cl.launch_count() == (14 + 12 if expand == 0 else 14)
+        assert cl.launch_count() == (13 + 12 if expand == 0 else 13)
 
 
 def test_paper_parameter_workload(clue_mod):
