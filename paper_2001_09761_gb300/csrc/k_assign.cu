@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) k_link(Buffers b, Params p) {
                     }
                 }
             }
+            if (p.chase) continue;  // no expansion lists to fill
             int n_root;
             const int r = block_incl_scan(root, ws, &n_root) - root;
             if (n_root) {

@@ -68,21 +68,36 @@ __global__ void __launch_bounds__(1024) k_scan_mid(T *partials, int64_t ntiles, 
     }
 }
 
+// Tile scan plus offset: warp w of the CTA owns the tile's w-th run of
+// 32 * SCAN_ITEMS elements, read in coalesced rows of 32 and scanned with
+// warp shuffles; one CTA-wide step adds the earlier warps' totals.
 template <typename T, typename Load>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(Load ld, int64_t n, const T *partials,
                                                             T *out, int64_t ntiles) {
-    __shared__ T ws[32];
+    __shared__ T wsum[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t base = t * SCAN_TILE;
-        T carry = partials[t];
+        const int64_t base = t * SCAN_TILE + (int64_t)warp * 32 * SCAN_ITEMS;
+        T ex[SCAN_ITEMS];
+        T run = 0;  // the warp's running total
+#pragma unroll
         for (int i = 0; i < SCAN_ITEMS; ++i) {
-            const int64_t idx = base + (int64_t)i * SCAN_THREADS + threadIdx.x;
+            const int64_t idx = base + (int64_t)i * 32 + lane;
             const T v = idx < n ? ld(idx) : T(0);
-            T total;
-            const T incl = block_incl_scan(v, ws, &total);
-            if (idx < n) out[idx] = carry + incl - v;
-            carry += total;
+            const T incl = warp_incl_scan(v);
+            ex[i] = run + incl - v;
+            run += __shfl_sync(FULL_MASK, incl, 31);
         }
+        if (lane == 0) wsum[warp] = run;
+        __syncthreads();
+        T off = partials[t];
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const int64_t idx = base + (int64_t)i * 32 + lane;
+            if (idx < n) out[idx] = off + ex[i];
+        }
+        __syncthreads();  // wsum is reused by the next tile
     }
 }
 
