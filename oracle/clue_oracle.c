@@ -147,23 +147,30 @@ static void exact_add(uint32_t acc[EXACT_LIMBS], float t)
     /* |t| = mant * 2^(shift - 149): subnormals have e = 0, mant = frac */
     const uint64_t mant = e ? (frac | 0x800000u) : frac;
     const int shift = e ? (int)e - 1 : 0;
-    uint32_t add[EXACT_LIMBS] = {0};
-    const uint64_t v = mant << (shift % 32);       /* below 2^56: two limbs */
-    add[shift / 32] = (uint32_t)v;
-    add[shift / 32 + 1] = (uint32_t)(v >> 32);
-    if (bits >> 31) {                              /* negative: add -|t| */
-        uint64_t carry = 1;
-        for (int k = 0; k < EXACT_LIMBS; ++k) {
-            const uint64_t s = (uint64_t)(uint32_t)~add[k] + carry;
-            add[k] = (uint32_t)s;
+    const int k = shift / 32;
+    const uint64_t v = mant << (shift % 32);       /* below 2^56: limbs k, k+1 */
+    const uint32_t part[2] = {(uint32_t)v, (uint32_t)(v >> 32)};
+    if (!(bits >> 31)) {
+        /* add |t| at limbs k, k+1, then the carry upwards */
+        uint64_t carry = 0;
+        for (int i = k; i < EXACT_LIMBS; ++i) {
+            const uint64_t s = (uint64_t)acc[i] + (i - k < 2 ? part[i - k] : 0u) + carry;
+            acc[i] = (uint32_t)s;
             carry = s >> 32;
+            if (i > k && !carry)
+                break;
         }
-    }
-    uint64_t carry = 0;
-    for (int k = 0; k < EXACT_LIMBS; ++k) {
-        const uint64_t s = (uint64_t)acc[k] + add[k] + carry;
-        acc[k] = (uint32_t)s;
-        carry = s >> 32;
+    } else {
+        /* subtract |t| at limbs k, k+1, then the borrow upwards (two's
+         * complement: a borrow out of the top limb wraps) */
+        uint64_t borrow = 0;
+        for (int i = k; i < EXACT_LIMBS; ++i) {
+            const uint64_t sub = (uint64_t)(i - k < 2 ? part[i - k] : 0u) + borrow;
+            borrow = (uint64_t)acc[i] < sub;
+            acc[i] = (uint32_t)((uint64_t)acc[i] - sub);
+            if (i > k && !borrow)
+                break;
+        }
     }
 }
 
@@ -185,11 +192,12 @@ static float exact_round(const uint32_t acc[EXACT_LIMBS])
         carry = s >> 32;
     }
     int p = -1;                                    /* highest set bit */
-    for (int i = 32 * EXACT_LIMBS - 1; i >= 0; --i)
-        if (bit_at(mag, i)) {
-            p = i;
-            break;
-        }
+    for (int k = EXACT_LIMBS - 1; k >= 0 && p < 0; --k)
+        for (int b = 31; b >= 0 && mag[k]; --b)
+            if ((mag[k] >> b) & 1u) {
+                p = 32 * k + b;
+                break;
+            }
     if (p < 0)
         return 0.0f;
     uint32_t bits;
@@ -203,9 +211,10 @@ static float exact_round(const uint32_t acc[EXACT_LIMBS])
         for (int b = 0; b < 24; ++b)
             m |= (uint32_t)bit_at(mag, sh + b) << b;
         const int guard = bit_at(mag, sh - 1);
-        int sticky = 0;
-        for (int b = 0; b < sh - 1; ++b)
-            sticky |= bit_at(mag, b);
+        int sticky = 0;                            /* any bit below the guard bit */
+        for (int k = 0; k < (sh - 1) / 32; ++k)
+            sticky |= mag[k] != 0;
+        sticky |= (mag[(sh - 1) / 32] & ((1u << ((sh - 1) % 32)) - 1u)) != 0;
         if (guard && (sticky || (m & 1u))) {
             m += 1;
             if (m == (1u << 24)) {
