@@ -235,7 +235,8 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     b.code = b.key;  // the cell of each hit is dead once the ids are scattered
     b.fcount = (int32_t *)take(n * 4);
     b.hs = (unsigned long long *)take((n + 1) * 8);
-    b.srank = (int32_t *)b.hs;
+    b.sbits = (uint32_t *)b.hs;  // chase mode: the seed bits and their word scan
+    b.sword = (int32_t *)(b.sbits + (n / 32 + 8));
     b.fol = (int32_t *)take(n * 4);
     b.seed_list = (int32_t *)take(n * 4);
     b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
@@ -355,6 +356,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     };
     CK(cudaMemsetAsync(&b.ctrl->overflow, 0, sizeof(Ctrl) - sizeof(unsigned), s));
     CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
+    if (p.chase) CK(cudaMemsetAsync(b.sbits, 0, (size_t)(b.N / 32 + 1) * 4, s));
     CK(rec(nullptr));
     CK(launch_fill_count(b, p, cfg, s));
     CK(rec("fill_count"));

@@ -102,7 +102,9 @@ struct Buffers {
     int32_t *fcount;     // [N] followers per hit (zeroed in the fill step)
     int32_t *frank;      // [N] arrival rank of a follower in its nh's list (aliases rank)
     unsigned long long *hs;  // [N + 1] exclusive scan of (seed << 32 | followers)
-    int32_t *srank;      // [N + 1] exclusive scan of seed flags (chase mode; aliases hs)
+    uint32_t *sbits;     // [N / 32 + 1] seed flags by hit, one bit each (chase mode;
+                         //     aliases hs; zeroed per run)
+    int32_t *sword;      // [N / 32 + 2] exclusive scan of the words' seed counts
     int32_t *fol;        // [N] follower lists (CSR by nh)
     int32_t *seed_list;  // [N] seeds by global seed rank
     int32_t *front_a;    // [N] expansion frontiers (alias perm / tmp, free after S1)

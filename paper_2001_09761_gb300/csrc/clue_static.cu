@@ -143,7 +143,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.code = b.key;
     b.fcount = (int32_t *)take(NB * 4);
     b.hs = (unsigned long long *)take((NB + 1) * 8);
-    b.srank = (int32_t *)b.hs;
+    b.sbits = (uint32_t *)b.hs;  // chase mode: the seed bits and their word scan
+    b.sword = (int32_t *)(b.sbits + (NB / 32 + 8));
     b.fol = (int32_t *)take(NB * 4);
     b.seed_list = (int32_t *)take(NB * 4);
     b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted

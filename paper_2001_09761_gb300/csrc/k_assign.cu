@@ -24,18 +24,23 @@ struct LoadPacked {
     }
 };
 
-// Chase mode needs no follower lists: the seed ranks alone, as 32-bit values.
-struct LoadSeed {
-    const int32_t *code;
-    __device__ __forceinline__ int32_t operator()(int64_t i) const {
-        return code[i] == CODE_SEED;
-    }
+// Chase mode needs no follower lists, only seed ranks: the nh step sets one
+// bit per seed, and the scan runs over the words' bit counts.
+struct LoadSeedWord {
+    const uint32_t *bits;
+    __device__ __forceinline__ int32_t operator()(int64_t i) const { return __popc(bits[i]); }
 };
+
+// Rank of hit g among the batch's seeds (the seeds before it in hit order).
+__device__ __forceinline__ int seed_rank(const Buffers &b, int64_t g) {
+    const unsigned below = (1u << (g & 31)) - 1u;
+    return b.sword[g >> 5] + __popc(b.sbits[g >> 5] & below);
+}
 
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c,
                              cudaStream_t s, int *launches) {
     if (p.chase)
-        return exclusive_scan<int32_t>(LoadSeed{b.code}, b.N, b.srank,
+        return exclusive_scan<int32_t>(LoadSeedWord{b.sbits}, b.N / 32 + 1, b.sword,
                                        (int32_t *)b.scan_partials, c.grid_cap, s, launches);
     return exclusive_scan<unsigned long long>(LoadPacked{b.code, b.fcount}, b.N, b.hs,
                                               (unsigned long long *)b.scan_partials, c.grid_cap,
@@ -53,7 +58,7 @@ __global__ void __launch_bounds__(256) k_link(Buffers b, Params p) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int64_t hoff = b.events[tl.event].hit_off;
-        const unsigned ebase = p.chase ? (unsigned)b.srank[hoff] : (unsigned)(b.hs[hoff] >> 32);
+        const unsigned ebase = p.chase ? (unsigned)seed_rank(b, hoff) : (unsigned)(b.hs[hoff] >> 32);
         for (int k0 = 0; k0 < tl.len; k0 += blockDim.x) {
             const int k = k0 + threadIdx.x;
             int root = 0;
@@ -62,7 +67,7 @@ __global__ void __launch_bounds__(256) k_link(Buffers b, Params p) {
                 const int code = b.code[g];
                 if (code == CODE_SEED) {
                     if (p.chase) {
-                        b.cid[g] = (int32_t)((unsigned)b.srank[g] - ebase);
+                        b.cid[g] = (int32_t)((unsigned)seed_rank(b, g) - ebase);
                     } else {
                         const unsigned long long hg = b.hs[g];
                         b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);

@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) {
             const int code = seed ? CODE_SEED : outl ? CODE_OUTLIER : (nhj >= 0 ? nhj : CODE_NOISE);
             const int g = id_of(me);
             b.code[g] = code;
+            if (p.chase && seed) atomicOr(&b.sbits[g >> 5], 1u << (g & 31));
             if (!p.chase && code >= 0) b.frank[g] = atomicAdd(&b.fcount[code], 1);
         }
     }
