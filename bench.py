@@ -177,7 +177,7 @@ ALG_BYTES = {
     "rho": 16 + 4 + 4,                 # x, y, w, id, layer in; rho out
     "nh_delta": 16 + 4 + 4 + 8,        # x, y, rho, id, layer in; code, (delta^2, nh) out
     "link": 4 + 4 + 4 + 1,             # code, seed rank in; id, seed flag out
-    "chase": 4 + 4 + 4,                # code, id in; id out
+    "assign": 4 + 4 + 4 + 1,           # code, the nh's code, seed bits in; id, seed flag out
     "expand_level": 8 + 4 + 4 + 4,     # list range, parent id, follower in; id out
     "complete": 4 + 4,                 # id in, id out
 }

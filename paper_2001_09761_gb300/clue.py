@@ -208,8 +208,8 @@ def clue_stage_times(ctx, back=0):
 STAGE_OF = {"fill_count": "grid_fill", "scan_cells": "grid_fill", "fill_scatter": "grid_fill",
             "fill_canon": "grid_fill", "rho": "rho",
             "nh_delta": "nh_delta",
-            "scan_hits": "decide_followers", "link": "decide_followers",
-            "expand_level": "expand", "complete": "expand", "chase": "expand"}
+            "scan_hits": "decide_followers", "link": "decide_followers", "assign": "expand",
+            "expand_level": "expand", "complete": "expand"}
 
 
 def clue_last_launch_count(ctx) -> int:

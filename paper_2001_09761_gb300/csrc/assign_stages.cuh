@@ -1,0 +1,147 @@
+// Steps S4 and S5: seed ids and follower lists (Sec. 2.2, Eq. 5, Algorithm 3)
+// and the expansion of cluster ids down the followers: the bodies of the
+// link and chase stages, which the kernels in k_assign.cu wrap.  The seed / outlier
+// decision itself is taken by the nh step, which stores one code per hit.
+//
+// The paper appends seeds and followers with atomics (conflicts (ii) and (iii)
+// of Sec. 3), so seed numbering depends on thread timing.  Here seed ids are
+// ranks from a prefix sum over hit order, giving Algorithm 3's k++ numbering
+// (ascending seed index per event), and the follower lists are a CSR built by
+// the same prefix sum.  Expansion is k-way parallel as in the paper, one launch
+// per level of the frontier over all seeds' follower trees at once.
+#pragma once
+
+#include <climits>
+
+#include "scan.cuh"
+
+namespace clue {
+
+
+// (is_seed << 32 | follower count): one scan gives both the global seed rank
+// (high word) and the follower-list offset (low word) of every hit.
+struct LoadPacked {
+    const int32_t *code;
+    const int32_t *fcount;
+    __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
+        return ((unsigned long long)(code[i] == CODE_SEED) << 32) | (unsigned)fcount[i];
+    }
+};
+
+// Chase mode needs no follower lists, only seed ranks: the nh step sets one
+// bit per seed, and the scan runs over the words' bit counts.
+struct LoadSeedWord {
+    const uint32_t *bits;
+    __device__ __forceinline__ int32_t operator()(int64_t i) const { return __popc(bits[i]); }
+};
+
+// Rank of hit g among the batch's seeds (the seeds before it in hit order).
+__device__ __forceinline__ int seed_rank(const Buffers &b, int64_t g) {
+    const unsigned below = (1u << (g & 31)) - 1u;
+    return b.sword[g >> 5] + __popc(b.sbits[g >> 5] & below);
+}
+
+// Seeds take their per-event id; seeds with followers enter the first
+// frontier of the expansion (one atomic per CTA); followers enter the CSR list
+// of their nearest-higher at the rank the decision step's count returned
+// (order inside a list is irrelevant: each follower has exactly one parent);
+// everything else is noise for now.
+__device__ __forceinline__ void link_stage(const Buffers &b, const Params &p) {
+    __shared__ int ws[32];
+    __shared__ int s_base;
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+        const Tile tl = b.tiles[t];
+        const int64_t hoff = b.events[tl.event].hit_off;
+        const unsigned ebase = p.chase ? (unsigned)seed_rank(b, hoff) : (unsigned)(b.hs[hoff] >> 32);
+        for (int k0 = 0; k0 < tl.len; k0 += blockDim.x) {
+            const int k = k0 + threadIdx.x;
+            int root = 0;
+            if (k < tl.len) {
+                const int g = tl.start + k;
+                const int code = b.code[g];
+                if (code == CODE_SEED) {
+                    if (p.chase) {
+                        b.cid[g] = (int32_t)((unsigned)seed_rank(b, g) - ebase);
+                    } else {
+                        const unsigned long long hg = b.hs[g];
+                        b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);
+                        root = (unsigned)b.hs[g + 1] != (unsigned)hg;  // has followers
+                    }
+                    b.is_seed[g] = 1;
+                } else {
+                    b.is_seed[g] = 0;
+                    if (code >= 0) {  // a follower of nh = code
+                        if (!p.chase) b.fol[(int)(unsigned)b.hs[code] + b.frank[g]] = g;
+                        b.cid[g] = PENDING;
+                    } else {
+                        b.cid[g] = -1;
+                    }
+                }
+            }
+            if (p.chase) continue;  // no expansion lists to fill
+            int n_root;
+            const int r = block_incl_scan(root, ws, &n_root) - root;
+            if (n_root) {
+                if (threadIdx.x == 0) s_base = atomicAdd(&b.ctrl->fsize[0], n_root);
+                __syncthreads();
+                if (root) b.seed_list[s_base + r] = tl.start + k;
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// Chase mode (CLUE_EXPAND_CHASE): ids in one pass, with no follower lists and
+// no id read that another thread writes.  Every hit walks its chain of codes
+// (a follower's code is its nearest-higher) up to the first hit that is not a
+// follower, and takes that hit's id: a seed's rank among its event's seeds
+// (from the seed bits), or -1 at an outlier or at a hit with no nearest-higher
+// -- the closed form "a follower inherits the id of its nearest-higher" of
+// Algorithm 3's expansion.  A seed's chain is the seed itself.  Chains are
+// finite because rho rises strictly along them; the walk is still bounded by
+// N steps.
+__device__ __forceinline__ void assign_stage(const Buffers &b) {
+    constexpr int U = 4;  // hits in flight per thread: their walks overlap
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+        const Tile tl = b.tiles[t];
+        const int ebase = seed_rank(b, b.events[tl.event].hit_off);
+        for (int k0 = threadIdx.x; k0 < tl.len; k0 += U * blockDim.x) {
+            int v[U], c[U];
+            bool act[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = k0 + u * (int)blockDim.x;
+                act[u] = k < tl.len;
+                v[u] = tl.start + (act[u] ? k : 0);
+                c[u] = act[u] ? b.code[v[u]] : CODE_NOISE;
+                if (act[u]) b.is_seed[v[u]] = c[u] == CODE_SEED;
+            }
+            int64_t steps = 0;
+            bool any = true;
+            while (any && steps <= b.N) {
+                any = false;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (c[u] >= 0) {  // v[u] is a follower of c[u]
+                        v[u] = c[u];
+                        c[u] = b.code[v[u]];
+                        any = true;
+                    }
+                ++steps;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!act[u]) continue;
+                int id = -1;
+                if (c[u] == CODE_SEED) {
+                    id = seed_rank(b, v[u]) - ebase;
+                } else if (c[u] >= 0) {
+                    atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
+                }
+                b.cid[tl.start + k0 + u * (int)blockDim.x] = id;
+            }
+        }
+    }
+}
+
+}  // namespace clue

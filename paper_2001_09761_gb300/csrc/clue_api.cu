@@ -373,13 +373,13 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(rec("nh_delta"));
     CK(launch_scan_hits(b, p, cfg, s, &nl));
     CK(rec("scan_hits"));
-    CK(launch_link(b, p, cfg, s));
-    CK(rec("link"));
     if (p.chase) {
-        CK(launch_chase(b, cfg, s));
-        CK(rec("chase"));
-        nl += 4;  // rho, nh (with the decision), link, chase
+        CK(launch_assign(b, cfg, s));
+        CK(rec("assign"));
+        nl += 3;  // rho, nh (with the decision), assign
     } else {
+        CK(launch_link(b, p, cfg, s));
+        CK(rec("link"));
         for (int level = 0; level < EXPAND_LEVELS; ++level) {
             CK(launch_expand_level(b, cfg, level, s));
             CK(rec("expand_level"));
@@ -614,6 +614,7 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
         o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0 ||
         (o.expand != CLUE_EXPAND_FRONTIER && o.expand != CLUE_EXPAND_CHASE) ||
         o.chi < CLUE_CHI_FLAT || o.chi > CLUE_CHI_EXPONENTIAL || o.max_scratch_bytes < 0 ||
+
         (o.chi != CLUE_CHI_FLAT && !(o.chi_param > 0.0f && std::isfinite(o.chi_param))))
         return CLUE_ERR_ARG;
     clue_ctx *ctx = new (std::nothrow) clue_ctx();

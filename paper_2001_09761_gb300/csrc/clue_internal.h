@@ -132,7 +132,7 @@ cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cud
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s,
                              int *launches);
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_chase(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_assign(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);  // all levels
 cudaError_t launch_expand_level(const Buffers &b, const LaunchCfg &c, int level, cudaStream_t s);
 cudaError_t launch_complete(const Buffers &b, const LaunchCfg &c, cudaStream_t s);

@@ -1,41 +1,9 @@
-// Steps S4 and S5: seed ids and follower lists (Sec. 2.2, Eq. 5, Algorithm 3)
-// and the expansion of cluster ids down the followers.  The seed / outlier
-// decision itself is taken by the nh step, which stores one code per hit.
-//
-// The paper appends seeds and followers with atomics (conflicts (ii) and (iii)
-// of Sec. 3), so seed numbering depends on thread timing.  Here seed ids are
-// ranks from a prefix sum over hit order, giving Algorithm 3's k++ numbering
-// (ascending seed index per event), and the follower lists are a CSR built by
-// the same prefix sum.  Expansion is k-way parallel as in the paper, one launch
-// per level of the frontier over all seeds' follower trees at once.
-#include <climits>
-
-#include "scan.cuh"
+// Steps S4 and S5 as per-stage kernels (link, chase; the frontier expansion
+// and the completion pass); the link and chase bodies and the description of
+// the seed numbering are in assign_stages.cuh.
+#include "assign_stages.cuh"
 
 namespace clue {
-
-// (is_seed << 32 | follower count): one scan gives both the global seed rank
-// (high word) and the follower-list offset (low word) of every hit.
-struct LoadPacked {
-    const int32_t *code;
-    const int32_t *fcount;
-    __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
-        return ((unsigned long long)(code[i] == CODE_SEED) << 32) | (unsigned)fcount[i];
-    }
-};
-
-// Chase mode needs no follower lists, only seed ranks: the nh step sets one
-// bit per seed, and the scan runs over the words' bit counts.
-struct LoadSeedWord {
-    const uint32_t *bits;
-    __device__ __forceinline__ int32_t operator()(int64_t i) const { return __popc(bits[i]); }
-};
-
-// Rank of hit g among the batch's seeds (the seeds before it in hit order).
-__device__ __forceinline__ int seed_rank(const Buffers &b, int64_t g) {
-    const unsigned below = (1u << (g & 31)) - 1u;
-    return b.sword[g >> 5] + __popc(b.sbits[g >> 5] & below);
-}
 
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c,
                              cudaStream_t s, int *launches) {
@@ -47,55 +15,7 @@ cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg 
                                               s, launches);
 }
 
-// Seeds take their per-event id; seeds with followers enter the first
-// frontier of the expansion (one atomic per CTA); followers enter the CSR list
-// of their nearest-higher at the rank the decision step's count returned
-// (order inside a list is irrelevant: each follower has exactly one parent);
-// everything else is noise for now.
-__global__ void __launch_bounds__(256) k_link(Buffers b, Params p) {
-    __shared__ int ws[32];
-    __shared__ int s_base;
-    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-        const Tile tl = b.tiles[t];
-        const int64_t hoff = b.events[tl.event].hit_off;
-        const unsigned ebase = p.chase ? (unsigned)seed_rank(b, hoff) : (unsigned)(b.hs[hoff] >> 32);
-        for (int k0 = 0; k0 < tl.len; k0 += blockDim.x) {
-            const int k = k0 + threadIdx.x;
-            int root = 0;
-            if (k < tl.len) {
-                const int g = tl.start + k;
-                const int code = b.code[g];
-                if (code == CODE_SEED) {
-                    if (p.chase) {
-                        b.cid[g] = (int32_t)((unsigned)seed_rank(b, g) - ebase);
-                    } else {
-                        const unsigned long long hg = b.hs[g];
-                        b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);
-                        root = (unsigned)b.hs[g + 1] != (unsigned)hg;  // has followers
-                    }
-                    b.is_seed[g] = 1;
-                } else {
-                    b.is_seed[g] = 0;
-                    if (code >= 0) {  // a follower of nh = code
-                        if (!p.chase) b.fol[(int)(unsigned)b.hs[code] + b.frank[g]] = g;
-                        b.cid[g] = PENDING;
-                    } else {
-                        b.cid[g] = -1;
-                    }
-                }
-            }
-            if (p.chase) continue;  // no expansion lists to fill
-            int n_root;
-            const int r = block_incl_scan(root, ws, &n_root) - root;
-            if (n_root) {
-                if (threadIdx.x == 0) s_base = atomicAdd(&b.ctrl->fsize[0], n_root);
-                __syncthreads();
-                if (root) b.seed_list[s_base + r] = tl.start + k;
-                __syncthreads();
-            }
-        }
-    }
-}
+__global__ void __launch_bounds__(256) k_link(Buffers b, Params p) { link_stage(b, p); }
 
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
     const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
@@ -103,58 +23,11 @@ cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, c
     return cudaGetLastError();
 }
 
-// Expansion by chasing (CLUE_EXPAND_CHASE): every follower still pending
-// follows its nh chain up to the first hit with a final id -- a seed's id, an
-// id another thread already resolved (a benign race: a pending entry reads as
-// pending or as its final value), or -1 at an outlier or a hit with no
-// nearest-higher -- and takes it: the closed form "a follower inherits the id
-// of its nearest-higher".  The chain is finite because rho rises strictly
-// along it; the walk is still bounded by N steps.
-__global__ void __launch_bounds__(256, 2) k_chase(Buffers b) {
-    constexpr int U = 4;  // hits in flight per thread: their walks overlap
-    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-        const Tile tl = b.tiles[t];
-        for (int k0 = threadIdx.x; k0 < tl.len; k0 += U * blockDim.x) {
-            int v[U], cv[U];
-            bool act[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int k = k0 + u * (int)blockDim.x;
-                act[u] = k < tl.len && b.cid[tl.start + k] == PENDING;
-                v[u] = act[u] ? b.code[tl.start + k] : 0;  // a pending hit is a follower
-                cv[u] = PENDING;
-            }
-            int64_t steps = 0;
-            bool any = true;
-            while (any && steps <= b.N) {
-                any = false;
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (act[u] && cv[u] == PENDING) cv[u] = b.cid[v[u]];
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (act[u] && cv[u] == PENDING) {
-                        v[u] = b.code[v[u]];
-                        any = true;
-                    }
-                ++steps;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (act[u]) {
-                    if (cv[u] == PENDING) {
-                        atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
-                        cv[u] = -1;
-                    }
-                    b.cid[tl.start + k0 + u * (int)blockDim.x] = cv[u];
-                }
-        }
-    }
-}
+__global__ void __launch_bounds__(256, 2) k_assign(Buffers b) { assign_stage(b); }
 
-cudaError_t launch_chase(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
+cudaError_t launch_assign(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
     const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
-    k_chase<<<grid > 0 ? grid : 1, 256, 0, s>>>(b);
+    k_assign<<<grid > 0 ? grid : 1, 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 

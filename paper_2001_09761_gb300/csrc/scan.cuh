@@ -32,9 +32,10 @@ __device__ __forceinline__ T block_incl_scan(T v, T *ws, T *total) {
     return incl + add;
 }
 
+// The three stages as device functions, each wrapped by a kernel below.
 template <typename T, typename Load>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Load ld, int64_t n, T *partials,
-                                                              int64_t ntiles) {
+__device__ __forceinline__ void scan_reduce_stage(const Load &ld, int64_t n, T *partials,
+                                                  int64_t ntiles) {
     __shared__ T ws[32];
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t base = t * SCAN_TILE;
@@ -50,8 +51,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Load ld, int64_t n
     }
 }
 
+// One CTA (any multiple of 32 threads) scans the tile sums.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_scan_mid(T *partials, int64_t ntiles, T *out, int64_t n) {
+__device__ __forceinline__ void scan_mid_stage(T *partials, int64_t ntiles, T *out, int64_t n) {
     __shared__ T ws[32];
     T carry = 0;
     for (int64_t base = 0; base < ntiles; base += blockDim.x) {
@@ -72,8 +74,8 @@ __global__ void __launch_bounds__(1024) k_scan_mid(T *partials, int64_t ntiles, 
 // 32 * SCAN_ITEMS elements, read in coalesced rows of 32 and scanned with
 // warp shuffles; one CTA-wide step adds the earlier warps' totals.
 template <typename T, typename Load>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(Load ld, int64_t n, const T *partials,
-                                                            T *out, int64_t ntiles) {
+__device__ __forceinline__ void scan_down_stage(const Load &ld, int64_t n, const T *partials,
+                                                T *out, int64_t ntiles) {
     __shared__ T wsum[SCAN_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -101,12 +103,74 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(Load ld, int64_t n, 
     }
 }
 
+template <typename T, typename Load>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Load ld, int64_t n, T *partials,
+                                                              int64_t ntiles) {
+    scan_reduce_stage<T, Load>(ld, n, partials, ntiles);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_mid(T *partials, int64_t ntiles, T *out, int64_t n) {
+    scan_mid_stage<T>(partials, ntiles, out, n);
+}
+
+template <typename T, typename Load>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(Load ld, int64_t n, const T *partials,
+                                                            T *out, int64_t ntiles) {
+    scan_down_stage<T, Load>(ld, n, partials, out, ntiles);
+}
+
+// The whole scan in one CTA, tile after tile with a running carry: for inputs
+// of a few tiles, where three launches cost more than the work.
+template <typename T, typename Load>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(Load ld, int64_t n, T *out,
+                                                              int64_t ntiles) {
+    __shared__ T wsum[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T carry = 0;  // the same in every thread
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int64_t base = t * SCAN_TILE + (int64_t)warp * 32 * SCAN_ITEMS;
+        T ex[SCAN_ITEMS];
+        T run = 0;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const int64_t idx = base + (int64_t)i * 32 + lane;
+            const T v = idx < n ? ld(idx) : T(0);
+            const T incl = warp_incl_scan(v);
+            ex[i] = run + incl - v;
+            run += __shfl_sync(FULL_MASK, incl, 31);
+        }
+        if (lane == 0) wsum[warp] = run;
+        __syncthreads();
+        T off = carry, total = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+            off += w < warp ? wsum[w] : T(0);
+            total += wsum[w];
+        }
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const int64_t idx = base + (int64_t)i * 32 + lane;
+            if (idx < n) out[idx] = off + ex[i];
+        }
+        carry += total;
+        __syncthreads();  // wsum is reused by the next tile
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+constexpr int64_t SCAN_SINGLE_MAX_TILES = 2;
+
 // Exclusive scan of ld(0..n-1) into out[0..n-1], out[n] = total.
 // `partials` must hold scan_partials_needed(n) elements of T.
 template <typename T, typename Load>
 cudaError_t exclusive_scan(Load ld, int64_t n, T *out, T *partials, int grid_cap, cudaStream_t s,
                            int *launches) {
     const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (ntiles <= SCAN_SINGLE_MAX_TILES) {
+        k_scan_single<T, Load><<<1, SCAN_THREADS, 0, s>>>(ld, n, out, ntiles);
+        if (launches) *launches += 1;
+        return cudaGetLastError();
+    }
     const int grid = (int)(ntiles < grid_cap ? (ntiles > 0 ? ntiles : 1) : grid_cap);
     k_scan_reduce<T, Load><<<grid, SCAN_THREADS, 0, s>>>(ld, n, partials, ntiles);
     k_scan_mid<T><<<1, 1024, 0, s>>>(partials, ntiles, out, n);
