@@ -792,13 +792,25 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
             CK(cudaEventCreateWithFlags(&ctx->chunk_done[i], cudaEventDisableTiming));
         }
     }
-    // Split the batch at event boundaries into up to 8 chunks of about equal
-    // hits (at least 4M hits each), so that the copy of chunk c+1 in and the
-    // copy of chunk c-1 out overlap the clustering of chunk c.
-    const int64_t target = std::max<int64_t>(N / 8, 4 << 20);
+    // Split the batch at event boundaries into up to 8 chunks, so that the
+    // copy of chunk c+1 in and the copy of chunk c-1 out overlap the
+    // clustering of chunk c.  Only the first chunk's copy in and the last
+    // chunk's copy out are exposed, so those two are small (1/32 of the hits)
+    // and the six between them take 5/32 each; batches below 32M hits use
+    // fewer, larger chunks (at least 1M hits at the ends, 4M between).
     std::vector<int32_t> cuts{0};
-    for (int32_t e = 1; e < n_events && (int)cuts.size() < 8; ++e)
-        if (offsets[e] - offsets[cuts.back()] >= target) cuts.push_back(e);
+    if (N >= (int64_t)(32 << 20)) {
+        const int64_t at32[7] = {1, 6, 11, 16, 21, 26, 31};  // cut points, in N / 32
+        for (int k = 0; k < 7; ++k) {
+            int32_t e = cuts.back() + 1;
+            while (e < n_events && offsets[e] < N * at32[k] / 32) ++e;
+            if (e < n_events) cuts.push_back(e);
+        }
+    } else {
+        const int64_t target = std::max<int64_t>(N / 8, 4 << 20);
+        for (int32_t e = 1; e < n_events && (int)cuts.size() < 8; ++e)
+            if (offsets[e] - offsets[cuts.back()] >= target) cuts.push_back(e);
+    }
     cuts.push_back(n_events);
     // the previous call's output copies must be done before the buffers are reused
     CK(cudaStreamSynchronize(ctx->d2h));

@@ -247,6 +247,25 @@ def test_host_pointer_path_pipelined_chunks(clue_mod):
     assert np.array_equal(hcid[offs[5]:offs[6]], ref["cluster_id"])
 
 
+def test_host_pointer_path_tapered_chunks(clue_mod):
+    """A batch above 32M hits is cut into a small first chunk, six large ones
+    and a small last one; the results equal the device-pointer path's."""
+    base = [gen.make_event(n, 100, 2700 + i, "blobs")
+            for i, n in enumerate([1_300_000, 700_000, 2_100_000, 40_000, 900_000])]
+    evs = [base[i % len(base)] for i in range(34)]  # 34 events, about 34M hits
+    x, y, l, e, offs = gen.concat(evs)
+    assert offs[-1] >= 32 << 20
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    dcid, dseed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    cl.sync()
+    dcid, dseed = dcid.cpu().numpy(), dseed.cpu().numpy()
+    hcid, hseed = cl.run_batch_host(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    assert np.array_equal(hcid, dcid) and np.array_equal(hseed, dseed)
+    ref = oracle.run_event(base[3], gen.PARAMS_BLOBS, 100)
+    for i in (3, 28):  # the same small event in the second chunk and in the seventh
+        assert np.array_equal(hcid[offs[i]:offs[i + 1]], ref["cluster_id"])
+
+
 def test_edge_cases(clue_mod):
     cl = _cl(clue_mod, (-10.0, 10.0, -10.0, 10.0), 4)
     p = (1.0, 0.5, 1.0, 2.0)
