@@ -30,7 +30,8 @@ constexpr int64_t CLASS_EDGE[NCLASS + 1] = {0, 32768, 100000, 316228, 1000000, I
 constexpr int NPROF = 40;  // profiling events: one before the first kernel, one after each group
 constexpr int NPSETS = 4;  // profiled runs whose times stay readable (a ring of event sets)
 constexpr int NSTAGING = 4;
-constexpr size_t GRAPH_CACHE_MAX = 16;
+constexpr size_t GRAPH_CACHE_MAX = 32;
+constexpr int MAX_CHUNKS = 16;  // chunks of the host-pointer pipeline
 constexpr int64_t MAX_HITS = 2147483646LL;
 
 int class_of(int64_t n) {
@@ -84,7 +85,7 @@ struct clue_ctx {
     cudaStream_t own = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t h2d = nullptr, d2h = nullptr;  // copy streams of the host-pointer path
-    cudaEvent_t chunk_in[8] = {}, chunk_done[8] = {};
+    cudaEvent_t chunk_in[MAX_CHUNKS] = {}, chunk_done[MAX_CHUNKS] = {};
     char *arena = nullptr;
     size_t arena_cap = 0;
     void *dtables = nullptr;
@@ -680,7 +681,7 @@ void clue_destroy(clue_ctx *ctx) {
         cudaStreamSynchronize(ctx->d2h);
         cudaStreamDestroy(ctx->h2d);
         cudaStreamDestroy(ctx->d2h);
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < MAX_CHUNKS; ++i) {
             cudaEventDestroy(ctx->chunk_in[i]);
             cudaEventDestroy(ctx->chunk_done[i]);
         }
@@ -787,29 +788,35 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
     if (!ctx->h2d) {
         CK(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking));
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < MAX_CHUNKS; ++i) {
             CK(cudaEventCreateWithFlags(&ctx->chunk_in[i], cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&ctx->chunk_done[i], cudaEventDisableTiming));
         }
     }
-    // Split the batch at event boundaries into up to 8 chunks, so that the
-    // copy of chunk c+1 in and the copy of chunk c-1 out overlap the
-    // clustering of chunk c.  Only the first chunk's copy in and the last
-    // chunk's copy out are exposed, so those two are small (1/32 of the hits)
-    // and the six between them take 5/32 each; batches below 32M hits use
-    // fewer, larger chunks (at least 1M hits at the ends, 4M between).
+    // Split the batch at event boundaries into chunks, so that the copy of
+    // chunk c+1 in and the copy of chunk c-1 out overlap the clustering of
+    // chunk c.  A chunk's copy in (16 B/hit over the host link, about 13G
+    // hits/s) must end before the previous chunk's clustering (about 9G
+    // hits/s) or the device waits, so chunks grow by 1.25x from a small first
+    // one (its copy is exposed) up to N/6; the last one is again small (its
+    // copy out is exposed).  Batches below 8M hits are one chunk.
     std::vector<int32_t> cuts{0};
-    if (N >= (int64_t)(32 << 20)) {
-        const int64_t at32[7] = {1, 6, 11, 16, 21, 26, 31};  // cut points, in N / 32
-        for (int k = 0; k < 7; ++k) {
+    if (N >= (int64_t)(8 << 20)) {
+        double want = std::max(N / 64.0, (double)(1 << 20));
+        const double cap = N / 6.0;
+        const int64_t tail = N / 32;  // hits kept for the last chunk
+        int64_t at = 0;
+        while ((int)cuts.size() < MAX_CHUNKS - 1) {
+            const int64_t target = std::min(at + (int64_t)want, N - tail);
+            if (target <= at) break;
             int32_t e = cuts.back() + 1;
-            while (e < n_events && offsets[e] < N * at32[k] / 32) ++e;
-            if (e < n_events) cuts.push_back(e);
+            while (e < n_events && offsets[e] < target) ++e;
+            if (e >= n_events) break;
+            cuts.push_back(e);
+            at = offsets[e];
+            if (at >= N - tail) break;
+            want = std::min(want * 1.25, cap);
         }
-    } else {
-        const int64_t target = std::max<int64_t>(N / 8, 4 << 20);
-        for (int32_t e = 1; e < n_events && (int)cuts.size() < 8; ++e)
-            if (offsets[e] - offsets[cuts.back()] >= target) cuts.push_back(e);
     }
     cuts.push_back(n_events);
     // the previous call's output copies must be done before the buffers are reused
