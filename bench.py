@@ -201,10 +201,15 @@ def parse_traffic():
 
 
 def source_hash():
+    """Hash of the kernel sources' code: comments and whitespace removed, so
+    that only a change to the code itself invalidates a traffic capture."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in sorted((ROOT / "paper_2001_09761_gb300" / "csrc").glob("*")):
-        h.update(f.read_bytes())
+        code = re.sub(r"/\*.*?\*/", " ", f.read_text(), flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(f.name.encode() + b"\0" + " ".join(code.split()).encode())
     return h.hexdigest()[:12]
 
 

@@ -14,9 +14,10 @@
  *   - distances are compared squared in fp32: dx = x_j - x_i, dy = y_j - y_i,
  *     d2 = dx*dx + dy*dy, each operation rounded to nearest, no fused
  *     multiply-add; thresholds are squared once in fp32;
- *   - chi is flat unless clue_opts.chi says otherwise: rho_i is the fp32 sum,
- *     from +0 in ascending hit index j, of w_j (or fl(chi(d_ij) w_j)) over all
- *     hits j of i's layer with d2 < d_c^2 (j = i included);
+ *   - chi is flat unless clue_opts.chi says otherwise: rho_i is the exact sum
+ *     of w_j (or fl(chi(d_ij) w_j)) over all hits j of i's layer with
+ *     d2 < d_c^2 (j = i included), rounded once to the nearest fp32, ties to
+ *     even: a function of the neighbour set alone (Eq. 3 sums over a set);
  *   - nh_i is the hit j of i's layer with rho_j > rho_i and d2 < d_m^2,
  *     d_m = max(delta_c, delta_o), of smallest d2, the smaller index on a tie;
  *     -1 (and delta = +inf) when there is none;

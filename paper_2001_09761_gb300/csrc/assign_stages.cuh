@@ -1,14 +1,16 @@
-// Steps S4 and S5: seed ids and follower lists (Sec. 2.2, Eq. 5, Algorithm 3)
-// and the expansion of cluster ids down the followers: the bodies of the
-// link and chase stages, which the kernels in k_assign.cu wrap.  The seed / outlier
-// decision itself is taken by the nh step, which stores one code per hit.
+// Steps S4 and S5: seed ids (Sec. 2.2, Eq. 5, Algorithm 3) and the expansion
+// of cluster ids down the followers: the bodies of the link stage (frontier
+// mode) and the assign stage (chase mode), which the kernels in k_assign.cu
+// wrap.  The seed / outlier decision itself is taken by the nh step, which
+// stores one code per hit.
 //
 // The paper appends seeds and followers with atomics (conflicts (ii) and (iii)
 // of Sec. 3), so seed numbering depends on thread timing.  Here seed ids are
 // ranks from a prefix sum over hit order, giving Algorithm 3's k++ numbering
-// (ascending seed index per event), and the follower lists are a CSR built by
-// the same prefix sum.  Expansion is k-way parallel as in the paper, one launch
-// per level of the frontier over all seeds' follower trees at once.
+// (ascending seed index per event).  Frontier mode builds the follower lists
+// as a CSR from the same prefix sum and expands k-way as in the paper, one
+// launch per level of the frontier over all seeds' trees at once; chase mode
+// needs no lists (assign_stage below).
 #pragma once
 
 #include <climits>
@@ -16,7 +18,6 @@
 #include "scan.cuh"
 
 namespace clue {
-
 
 // (is_seed << 32 | follower count): one scan gives both the global seed rank
 // (high word) and the follower-list offset (low word) of every hit.

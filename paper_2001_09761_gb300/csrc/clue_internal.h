@@ -10,10 +10,8 @@ namespace clue {
 // an event; tile t covers [tiles[t].start, tiles[t].start + tiles[t].len).
 constexpr int TILE = 1024;
 
-// A cell segment longer than this is sorted by one CTA (radix) instead of by
-// per-slot ranking.
-
-// cluster id of a follower whose id has not been passed down yet.
+// Cluster id of a follower whose id has not been passed down yet (frontier
+// expansion).
 constexpr int32_t PENDING = -2;
 
 // Outcome of the decision step per hit (Sec. 2.2): a follower stores its
