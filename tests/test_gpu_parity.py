@@ -112,6 +112,42 @@ def test_parity_scaling_event_full_size(clue_mod):
     assert_parity(g, ref)
 
 
+def test_full_batch_in_the_bench_configuration(clue_mod):
+    """The benchmark's workload at full size (256 events, 65.2M hits) in its
+    launch configuration: autotuned bins, then a replayed CUDA graph.  Six
+    events spread over the size range are checked in full against the oracle
+    (every output, intermediates included); every event of the batch is
+    checked for the numbering of Algorithm 3 (seed ids 0..k-1 in ascending
+    seed index, every other id in [-1, k))."""
+    import torch
+    evs = gen.uneven_batch()
+    x, y, l, e, offs = gen.concat(evs)
+    n = int(offs[-1])
+    d = lambda a: torch.from_numpy(a).cuda()
+    tx, ty, tl, te = d(x), d(y), d(l), d(e)
+    cid = torch.empty(n, dtype=torch.int32, device="cuda")
+    seed = torch.empty(n, dtype=torch.uint8, device="cuda")
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    cl.autotune(tx, ty, tl, te, offs, gen.PARAMS_BLOBS, reps=1)
+    for _ in range(3):  # direct, captured, replayed
+        cl.run_batch(tx, ty, tl, te, offs, gen.PARAMS_BLOBS, out=(cid, seed))
+    rho, delta, nh = cl.intermediates()
+    cl.sync()
+    c, sd = cid.cpu().numpy(), seed.cpu().numpy()
+    order = np.argsort([ev.n for ev in evs])
+    for i in order[[0, 51, 102, 153, 204, 255]]:
+        a, z = int(offs[i]), int(offs[i + 1])
+        g = dict(cluster_id=c[a:z], is_seed=sd[a:z], rho=rho[a:z].cpu().numpy(),
+                 delta=delta[a:z].cpu().numpy(), nh=nh[a:z].cpu().numpy())
+        assert_parity(g, oracle.run_event(evs[i], gen.PARAMS_BLOBS, 100))
+    for i in range(len(evs)):
+        a, z = int(offs[i]), int(offs[i + 1])
+        ci, si = c[a:z], sd[a:z].astype(bool)
+        k = int(si.sum())
+        assert np.array_equal(ci[si], np.arange(k))
+        assert np.all((ci[~si] >= -1) & (ci[~si] < k))
+
+
 @pytest.mark.parametrize("bin_size,block", [(2.0, 128), (3.0, 256), (4.5, 64), (9.0, 256),
                                              (25.0, 128)])
 def test_bin_size_and_block_do_not_change_results(clue_mod, bin_size, block):
