@@ -33,7 +33,9 @@
  * Work is queued on the context's stream and returns before it finishes.
  * The context owns a grow-only scratch arena (allocated once per size, as the
  * paper's Sec. 4.2 allocates once before the event loop).  A context is used
- * by one host thread at a time.
+ * by one host thread at a time.  A run is refused (CLUE_ERR_STATE) while the
+ * caller is capturing the context's stream into a CUDA graph of its own: the
+ * library captures and replays repeated calls itself.
  *
  * Errors: every call returns CLUE_OK (0) or a CLUE_ERR_* code; nothing aborts
  * and nothing traps on the device.  Errors in the inputs (a NaN or infinite

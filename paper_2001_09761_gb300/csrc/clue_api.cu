@@ -20,6 +20,7 @@
 
 #include "clue.h"
 #include "clue_internal.h"
+#include "scan.cuh"
 
 using namespace clue;
 
@@ -107,6 +108,9 @@ struct clue_ctx {
     bool have_last = false;
     int last_launches = 0;
     std::vector<GraphEntry> graphs;
+    // one executable graph per pipeline shape, updated to each new call's
+    // parameters (calls whose exact signature is not cached)
+    std::unordered_map<int, cudaGraphExec_t> templates;
     std::unordered_map<uint64_t, int> seen;
     uint64_t tick = 0;
     char *hio = nullptr;
@@ -257,6 +261,9 @@ void drop_graphs(clue_ctx *ctx) {
     }
     ctx->graphs.clear();
     ctx->seen.clear();
+    for (auto &t : ctx->templates)
+        if (t.second) cudaGraphExecDestroy(t.second);
+    ctx->templates.clear();
 }
 
 int ensure_arena(clue_ctx *ctx, size_t need) {
@@ -449,6 +456,54 @@ uint64_t signature(const clue_ctx *ctx, const Plan &plan, const Buffers &b, cons
     return h;
 }
 
+// The shape of a run's launch sequence: expansion mode and, for each prefix
+// sum, whether it runs in one CTA (at most SCAN_SINGLE_MAX_TILES tiles).
+int pipeline_shape(const Buffers &b, const Params &p) {
+    auto one = [](int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE <= SCAN_SINGLE_MAX_TILES; };
+    const int64_t second = p.chase ? b.N / 32 + 1 : b.N;  // seed words / packed scan
+    return (p.chase ? 1 : 0) | (one(b.C) ? 2 : 0) | (one(second) ? 4 : 0);
+}
+
+// Queue a run whose exact signature has no cached graph: capture it, and
+// launch it through the executable graph of its shape, updated to this run's
+// parameters (one graph launch instead of a dozen API calls per run).
+int enqueue_via_template(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &cfg,
+                         int *launches) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    int erc = CLUE_OK;
+    if (e == cudaSuccess) {
+        erc = enqueue(ctx, b, p, cfg, launches);
+        e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (erc != CLUE_OK && e == cudaSuccess) e = cudaErrorUnknown;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e, "graph capture");
+    }
+    cudaGraphExec_t &ex = ctx->templates[pipeline_shape(b, p)];
+    bool updated = false;
+    if (ex) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(ex, graph, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(ex);
+            ex = nullptr;
+        }
+    }
+    if (!updated) e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ex = nullptr;
+        return cuda_fail(ctx, e, "graph instantiate");
+    }
+    CK(cudaGraphLaunch(ex, ctx->stream));
+    return CLUE_OK;
+}
+
 int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,
               const float *energy, const int64_t *offsets, int32_t E, float dc, float rhoc,
               float delta_c, float delta_o, int32_t *cid, uint8_t *is_seed, bool allow_graph) {
@@ -464,6 +519,15 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     if (N == 0) return CLUE_OK;
     if (!x || !y || !layer || !energy || !cid || !is_seed) return CLUE_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
+    // A caller's own stream capture would record the tables' copy from a
+    // reused staging buffer, which a later replay would read stale.
+    cudaStreamCaptureStatus outer = cudaStreamCaptureStatusNone;
+    if (ctx->stream) CK(cudaStreamIsCapturing(ctx->stream, &outer));
+    if (outer != cudaStreamCaptureStatusNone) {
+        ctx->msg = "the context's stream is being captured; run outside stream capture "
+                   "(repeated calls are captured and replayed by the library itself)";
+        return CLUE_ERR_STATE;
+    }
 
     Plan plan;
     rc = build_plan(ctx, offsets, E, dc, plan);
@@ -572,7 +636,8 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     if (rc) return rc;
     point_tables(b, plan, ctx->dtables);
     int launches = 0;
-    rc = enqueue(ctx, b, p, cfg, &launches);
+    rc = graphs && !ctx->profiling ? enqueue_via_template(ctx, b, p, cfg, &launches)
+                                   : enqueue(ctx, b, p, cfg, &launches);
     if (rc) return rc;
     ctx->last = b;
     ctx->last_cfg = cfg;

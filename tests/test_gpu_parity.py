@@ -253,6 +253,30 @@ def test_exact_rho_of_coincident_sets(clue_mod):
         assert_parity(g, ref)
 
 
+def test_calls_under_a_callers_capture_are_refused(clue_mod):
+    """While the caller captures the context's stream into a graph of its own,
+    a run is refused (CLUE_ERR_STATE) without touching the capture; outside it
+    the context works as before."""
+    import torch
+    ev = gen.make_event(20_000, 10, 91, "blobs")
+    d = lambda a: torch.from_numpy(a).cuda()
+    tx, ty, tl, te = d(ev.x), d(ev.y), d(ev.layer), d(ev.energy)
+    cid = torch.empty(ev.n, dtype=torch.int32, device="cuda")
+    seed = torch.empty(ev.n, dtype=torch.uint8, device="cuda")
+    cl = _cl(clue_mod, gen.EXTENT, 10)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cl.stream):
+        rc = clue_mod.clue_run(cl.ctx, tx.data_ptr(), ty.data_ptr(), tl.data_ptr(),
+                               te.data_ptr(), ev.n, *gen.PARAMS_BLOBS, cid.data_ptr(),
+                               seed.data_ptr())
+        cid.fill_(0)  # the caller's own captured work
+    assert rc == clue_mod.CLUE_ERR_STATE
+    assert "captured" in clue_mod.clue_last_message(cl.ctx)
+    g.replay()
+    torch.cuda.synchronize()
+    assert_parity(_gpu_all(cl, ev, gen.PARAMS_BLOBS), oracle.run_event(ev, gen.PARAMS_BLOBS, 10))
+
+
 def test_host_pointer_path(clue_mod):
     evs = [gen.make_event(n, 100, 700 + i, "blobs") for i, n in enumerate([3000, 25000, 9000])]
     x, y, l, e, offs = gen.concat(evs)
