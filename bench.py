@@ -184,8 +184,8 @@ ALG_BYTES = {
 
 
 def parse_traffic():
-    """Per-kernel DRAM bytes per hit from the committed ncu summary, keyed by
-    kernel, with the source hash they were taken at (None if absent)."""
+    """Per-kernel (DRAM bytes per hit, source hash, issue-active share) from the
+    committed ncu summary, keyed by kernel."""
     p = ROOT / "profiles" / "traffic.md"
     out = {}
     if not p.exists():
@@ -194,19 +194,27 @@ def parse_traffic():
         f = [c.strip() for c in line.strip().strip("|").split("|")]
         if len(f) >= 4 and f[0] in ALG_BYTES:
             try:
-                out[f[0]] = (float(f[1]), f[3])
+                issue = float(f[4]) / 100 if len(f) >= 5 else None
+                out[f[0]] = (float(f[1]), f[3], issue)
             except ValueError:
                 pass
     return out
 
 
+# Host-side sources: a change there leaves the kernels' traffic unchanged.
+HOST_SOURCES = {"clue_api.cu", "clue_static.cu"}
+
+
 def source_hash():
-    """Hash of the kernel sources' code: comments and whitespace removed, so
-    that only a change to the code itself invalidates a traffic capture."""
+    """Hash of the kernel sources' code (every file of csrc but the host-side
+    ones), comments and whitespace removed, so that only a change to kernel
+    code invalidates a traffic capture."""
     import hashlib
     import re
     h = hashlib.sha256()
     for f in sorted((ROOT / "paper_2001_09761_gb300" / "csrc").glob("*")):
+        if f.name in HOST_SOURCES:
+            continue
         code = re.sub(r"/\*.*?\*/", " ", f.read_text(), flags=re.S)
         code = re.sub(r"//[^\n]*", " ", code)
         h.update(f.name.encode() + b"\0" + " ".join(code.split()).encode())
@@ -499,15 +507,19 @@ def main():
     dom = max((k for k in kern if k in ALG_BYTES), key=kern.get)
     peak, peak_kind = load_peaks()
     achieved = ALG_BYTES[dom] * N / (kern[dom] * 1e-3) / 1e9
-    traffic = None
+    traffic, issue = None, None
     tr = parse_traffic()
     if dom in tr and tr[dom][1] == source_hash():
         traffic = tr[dom][0] * N
+        issue = tr[dom][2]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
-                "alg_bytes_per_hit": ALG_BYTES[dom], "kernel_ms_per_step": kern,
-                "stage_ms_per_step": stages}
+                "alg_bytes_per_hit": ALG_BYTES[dom],
+                # ncu's share of cycles issuing an instruction (same capture as
+                # traffic): the density kernels are bound by issue, not bytes
+                "ncu_issue_active": issue,
+                "kernel_ms_per_step": kern, "stage_ms_per_step": stages}
 
     extra, srv = None, None
     if rank == 0 and not args.no_extra:
