@@ -220,17 +220,20 @@ def test_profiled_graph_replay_keeps_each_runs_times(clue_mod):
         assert np.array_equal(c[offs[i]:offs[i + 1]], ref["cluster_id"])
 
 
-def test_exact_rho_with_adversarial_weights(clue_mod):
+@pytest.mark.parametrize("chi,s", [(0, 0.0), (1, 1.0), (2, 0.8)])
+def test_exact_rho_with_adversarial_weights(clue_mod, chi, s):
     """Reading R4 on the GPU: weights over 1e-38..1e30, both signs,
     subnormals and zeros, so many windows fail the fast path's exactness
-    proof and take the integer accumulator; every output is bit-exact."""
+    proof and take the integer accumulator; every output is bit-exact, for
+    the flat, Gaussian and exponential kernels."""
     from exactsum import adversarial_weights
     ev = gen.make_event(30_000, 5, 77, "blobs")
     w = adversarial_weights(np.random.default_rng(5), ev.n)
-    cl = _cl(clue_mod, gen.EXTENT, 5)
+    cl = _cl(clue_mod, gen.EXTENT, 5, chi=chi, chi_param=s)
     ev2 = gen.Event(ev.x, ev.y, ev.layer, w)
     assert_parity(_gpu_all(cl, ev2, gen.PARAMS_BLOBS),
-                  oracle.run(ev.x, ev.y, ev.layer, w, gen.PARAMS_BLOBS, 5))
+                  oracle.run(ev.x, ev.y, ev.layer, w, gen.PARAMS_BLOBS, 5, chi=chi,
+                             chi_param=s))
 
 
 def test_exact_rho_of_coincident_sets(clue_mod):
