@@ -280,6 +280,32 @@ def test_calls_under_a_callers_capture_are_refused(clue_mod):
     assert_parity(_gpu_all(cl, ev, gen.PARAMS_BLOBS), oracle.run_event(ev, gen.PARAMS_BLOBS, 10))
 
 
+def test_distinct_events_back_to_back_through_graph_templates(clue_mod):
+    """Events new to the context, queued back to back with no sync between
+    them, all go through the same executable graph updated per call while
+    earlier launches may still run; every event's result is the oracle's."""
+    import torch
+    evs = [gen.make_event(n, 20, 300 + i, "blobs")
+           for i, n in enumerate([3000 + 997 * i for i in range(24)])]
+    x, y, l, e, offs = gen.concat(evs)
+    d = lambda a: torch.from_numpy(a).cuda()
+    tx, ty, tl, te = d(x), d(y), d(l), d(e)
+    n = int(offs[-1])
+    cid = torch.empty(n, dtype=torch.int32, device="cuda")
+    seed = torch.empty(n, dtype=torch.uint8, device="cuda")
+    cl = _cl(clue_mod, gen.EXTENT, 20, use_graphs=True)
+    for i in range(len(evs)):
+        a, z = int(offs[i]), int(offs[i + 1])
+        cl.run(tx[a:z], ty[a:z], tl[a:z], te[a:z], gen.PARAMS_BLOBS, out=(cid[a:z], seed[a:z]))
+    cl.sync()
+    c, sd = cid.cpu().numpy(), seed.cpu().numpy()
+    for i, ev in enumerate(evs):
+        ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 20)
+        a, z = int(offs[i]), int(offs[i + 1])
+        assert np.array_equal(c[a:z], ref["cluster_id"]), i
+        assert np.array_equal(sd[a:z], ref["is_seed"]), i
+
+
 def test_host_pointer_path(clue_mod):
     evs = [gen.make_event(n, 100, 700 + i, "blobs") for i, n in enumerate([3000, 25000, 9000])]
     x, y, l, e, offs = gen.concat(evs)
