@@ -373,6 +373,20 @@ def test_edge_cases(clue_mod):
     assert_parity(_gpu_all(cl, ev, p), oracle.run_event(ev, p, 4, extent=(-10.0, 10.0, -10.0, 10.0)))
 
 
+@pytest.mark.parametrize("params", [
+    (2.0, 2.0, 0.0, 0.0),      # d_m = 0: no nearest-higher search
+    (400.0, 2.0, 2.0, 4.0),    # d_c spans the layer: every hit neighbours every other
+    (2.0, -1.0, 2.0, 4.0),     # rho_c below every density: no outlier
+    (2.0, 1e30, 2.0, 4.0),     # rho_c above every density: no seed, all outliers or noise
+], ids=["dm0", "dc_huge", "rhoc_negative", "rhoc_huge"])
+def test_degenerate_parameters(clue_mod, params):
+    """The method's degenerate parameter choices, bit-exact against the oracle."""
+    ext = (-100.0, 100.0, -100.0, 100.0)
+    ev = gen.make_event(4000, 4, 61, "blobs", extent=ext)
+    cl = _cl(clue_mod, ext, 4)
+    assert_parity(_gpu_all(cl, ev, params), oracle.run_event(ev, params, 4, extent=ext))
+
+
 def test_dense_cells_and_exact_ties(clue_mod):
     """Thousands of hits in one bin (windows of thousands of candidates);
     identical coordinates give exact distance ties."""

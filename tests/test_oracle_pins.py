@@ -135,6 +135,23 @@ def test_invariants_on_generated_events(oracle_mod):
             assert cid[i] == (cid[j] if seed[j] else -1)
 
 
+@pytest.mark.parametrize("params", [(2.0, 2.0, 0.0, 0.0), (400.0, 2.0, 2.0, 4.0),
+                                    (2.0, -1.0, 2.0, 4.0), (2.0, 1e30, 2.0, 4.0)],
+                         ids=["dm0", "dc_huge", "rhoc_negative", "rhoc_huge"])
+def test_degenerate_parameters_match_brute_force(oracle_mod, params):
+    """No nearest-higher search (d_m = 0); d_c spanning the layer (every rho
+    of a layer equal, so every hit is a seed, Eq. 4 with R6); rho_c below or
+    above every density: oracle and brute force agree bit for bit."""
+    ext = (-100.0, 100.0, -100.0, 100.0)
+    ev = gen.make_event(600, 2, 61, "blobs", extent=ext)
+    o = oracle_mod.run_event(ev, params, 2, extent=ext)
+    _assert_same(o, brute_clue(ev.x, ev.y, ev.layer, ev.energy, params))
+    if params[0] == 400.0:
+        assert o["is_seed"].all() and (o["nh"] == -1).all()
+    if params[1] == 1e30:
+        assert not o["is_seed"].any() and (o["cluster_id"] == -1).all()
+
+
 def test_rho_is_exact_sum_rounded_once(oracle_mod):
     """Reading R4: rho_i is the exact rational sum of w_j over N_dc(i) rounded
     once to fp32 (ties to even), checked hit by hit with Python's exact
