@@ -171,6 +171,9 @@ def run_reference(args):
 # read once and every result written once (no re-reads, no scratch beyond
 # the stage's own outputs).
 ALG_BYTES = {
+    "fill_layers": 4 + 4,              # layer in; rank in the (event, layer) segment out
+    "fill_place": 16 + 4 + 16,         # x, y, w, layer, segment rank in; layered record out
+    "fill_cells": 16 + 16 + 4,         # layered record in; sorted record, layer out
     "fill_count": 16 + 4 + 4 + 4,      # x, y, w, layer in; cell, rank, cell count out
     "fill_scatter": 4 + 4 + 4 + 4,     # cell, rank, cell start in; hit id out
     "fill_canon": 4 + 16 + 16 + 4,     # id, packed record in; sorted hit, layer out

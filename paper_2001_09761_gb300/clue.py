@@ -205,7 +205,9 @@ def clue_stage_times(ctx, back=0):
 
 
 #: Pipeline step of each profiled kernel (S1 grid fill .. S5 expansion).
-STAGE_OF = {"fill_count": "grid_fill", "scan_cells": "grid_fill", "fill_scatter": "grid_fill",
+STAGE_OF = {"fill_layers": "grid_fill", "scan_segs": "grid_fill", "fill_place": "grid_fill",
+            "fill_cells": "grid_fill",
+            "fill_count": "grid_fill", "scan_cells": "grid_fill", "fill_scatter": "grid_fill",
             "fill_canon": "grid_fill", "rho": "rho",
             "nh_delta": "nh_delta",
             "scan_hits": "decide_followers", "link": "decide_followers", "assign": "expand",

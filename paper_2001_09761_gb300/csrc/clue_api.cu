@@ -64,6 +64,9 @@ struct Plan {
     std::vector<EventDesc> ev;
     std::vector<Tile> tiles;
     int64_t N = 0, C = 0;
+    int64_t nseg = 0;   // events x layers when the two-level sort applies, else 0
+    int64_t ntb = 0;    // tiles x layers (the two-level sort's run table), else 0
+    int max_cells = 0;  // most cells in one layer of the batch
 };
 
 uint64_t fnv(uint64_t h, const void *p, size_t n) {
@@ -209,13 +212,24 @@ int build_plan(clue_ctx *ctx, const int64_t *offsets, int32_t E, float dc, Plan 
     }
     plan.N = offsets[E];
     plan.C = C;
+    int64_t most = 0;
+    for (const EventDesc &d : plan.ev) most = std::max(most, (int64_t)d.nbx * d.nby);
+    plan.max_cells = (int)std::min<int64_t>(most, SEG_MAX_CELLS + 1);
+    // The two-level sort needs every layer's cells in one CTA's shared memory
+    // and a run table of tiles x layers of at most a few ints per hit.
+    const int64_t ntb = (int64_t)plan.tiles.size() * o.max_layers;
+    const bool seg = o.max_layers <= SEG_MAX_LAYERS && plan.max_cells <= SEG_MAX_CELLS &&
+                     ntb <= 4 * plan.N + (1 << 22);
+    plan.nseg = seg ? (int64_t)E * o.max_layers : 0;
+    plan.ntb = seg ? ntb : 0;
     return CLUE_OK;
 }
 
 // Carve the scratch arrays of a run out of the arena; grows the arena
 // (after draining the stream) when it is too small.  With `dry` set only the
 // size is computed.
-size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
+size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t nseg, int64_t ntb,
+             bool dry) {
     size_t off = 0;
     char *base = ctx->arena;
     auto take = [&](size_t bytes) -> void * {
@@ -237,7 +251,8 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     b.rec = (float4 *)take(n * 16);
     b.hr = (float2 *)b.rec;
     b.spr = (float4 *)take(n * 16);
-    b.code = b.key;  // the cell of each hit is dead once the ids are scattered
+    b.code = b.key;  // the cell of each hit is dead once the cells are sorted
+    b.cell16 = (unsigned short *)b.key;
     b.fcount = (int32_t *)take(n * 4);
     b.hs = (unsigned long long *)take((n + 1) * 8);
     b.sbits = (uint32_t *)b.hs;  // chase mode: the seed bits and their word scan
@@ -250,6 +265,10 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, bool dry) {
     const int64_t parts = std::max(scan_partials_needed(N), scan_partials_needed(C)) + 1;
     b.scan_partials = take((size_t)parts * 8);
     b.scan_partials_cap = parts;
+    b.nseg = nseg;
+    b.seg_cnt = nseg ? (int32_t *)take((size_t)nseg * 4) : nullptr;
+    b.seg_start = nseg ? (int32_t *)take((size_t)(nseg + 1) * 4) : nullptr;
+    b.tbase = ntb ? (int32_t *)take((size_t)ntb * 4) : nullptr;
     return off;
 }
 
@@ -300,6 +319,7 @@ void point_tables(Buffers &b, const Plan &plan, void *dtables) {
     b.nevents = (int32_t)plan.ev.size();
     b.N = plan.N;
     b.C = plan.C;
+    b.max_cells = plan.max_cells;
 }
 
 // Upload the plan tables through pinned staging (stream-ordered, so the host
@@ -363,17 +383,31 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
         return cudaEventRecordWithFlags(ctx->pev[set][ev++], s, rec_flags);
     };
     CK(cudaMemsetAsync(&b.ctrl->overflow, 0, sizeof(Ctrl) - sizeof(unsigned), s));
-    CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
+    if (b.nseg)
+        CK(cudaMemsetAsync(b.seg_cnt, 0, (size_t)b.nseg * 4, s));
+    else
+        CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
     if (p.chase) CK(cudaMemsetAsync(b.sbits, 0, (size_t)(b.N / 32 + 1) * 4, s));
     CK(rec(nullptr));
-    CK(launch_fill_count(b, p, cfg, s));
-    CK(rec("fill_count"));
-    CK(launch_scan_cells(b, cfg, s, &nl));
-    CK(rec("scan_cells"));
-    CK(launch_fill_scatter(b, cfg, s));
-    CK(rec("fill_scatter"));
-    CK(launch_fill_canon(b, cfg, s));
-    CK(rec("fill_canon"));
+    if (b.nseg) {  // two-level sort: layer segments, then cells
+        CK(launch_fill_layers(b, p, cfg, s));
+        CK(rec("fill_layers"));
+        CK(launch_scan_segs(b, cfg, s, &nl));
+        CK(rec("scan_segs"));
+        CK(launch_fill_place(b, p, cfg, s));
+        CK(rec("fill_place"));
+        CK(launch_fill_cells(b, p, b.max_cells, s));
+        CK(rec("fill_cells"));
+    } else {  // direct sort over all cells
+        CK(launch_fill_count(b, p, cfg, s));
+        CK(rec("fill_count"));
+        CK(launch_scan_cells(b, cfg, s, &nl));
+        CK(rec("scan_cells"));
+        CK(launch_fill_scatter(b, cfg, s));
+        CK(rec("fill_scatter"));
+        CK(launch_fill_canon(b, cfg, s));
+        CK(rec("fill_canon"));
+    }
     nl += 3;
     CK(launch_rho(b, p, cfg, s));
     CK(rec("rho"));
@@ -456,12 +490,14 @@ uint64_t signature(const clue_ctx *ctx, const Plan &plan, const Buffers &b, cons
     return h;
 }
 
-// The shape of a run's launch sequence: expansion mode and, for each prefix
-// sum, whether it runs in one CTA (at most SCAN_SINGLE_MAX_TILES tiles).
+// The shape of a run's launch sequence: expansion mode, form of the grid
+// fill and, for each prefix sum, whether it runs in one CTA (at most
+// SCAN_SINGLE_MAX_TILES tiles).
 int pipeline_shape(const Buffers &b, const Params &p) {
     auto one = [](int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE <= SCAN_SINGLE_MAX_TILES; };
+    const int64_t first = b.nseg ? b.nseg : b.C;          // segments / cells
     const int64_t second = p.chase ? b.N / 32 + 1 : b.N;  // seed words / packed scan
-    return (p.chase ? 1 : 0) | (one(b.C) ? 2 : 0) | (one(second) ? 4 : 0);
+    return (p.chase ? 1 : 0) | (one(first) ? 2 : 0) | (one(second) ? 4 : 0) | (b.nseg ? 8 : 0);
 }
 
 // Queue a run whose exact signature has no cached graph: capture it, and
@@ -533,10 +569,10 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     rc = build_plan(ctx, offsets, E, dc, plan);
     if (rc) return rc;
     Buffers b{};
-    const size_t need = carve(ctx, b, plan.N, plan.C, true);
+    const size_t need = carve(ctx, b, plan.N, plan.C, plan.nseg, plan.ntb, true);
     rc = ensure_arena(ctx, need);
     if (rc) return rc;
-    carve(ctx, b, plan.N, plan.C, false);
+    carve(ctx, b, plan.N, plan.C, plan.nseg, plan.ntb, false);
     b.x = x;
     b.y = y;
     b.w = energy;
@@ -687,7 +723,10 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
     if (!ctx) return CLUE_ERR_OOM;
     ctx->opts = o;
     ctx->device = o.device;
-    const float defaults[NCLASS] = {3.0f, 2.0f, 1.5f, 1.0f, 1.0f};
+    // Bin size in units of 2 d_c per event-size class: about one hit per cell
+    // or fewer for events spread over many layers (what the autotuner picks
+    // on such events); the smaller the event, the sparser its layers.
+    const float defaults[NCLASS] = {8.0f, 4.0f, 3.0f, 2.0f, 1.0f};
     for (int k = 0; k < NCLASS; ++k) ctx->bin_scale[k] = defaults[k];
     auto fail = [&](cudaError_t e, const char *what) {
         int rc = cuda_fail(ctx, e, what);
@@ -698,6 +737,8 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
     if (e != cudaSuccess) return fail(e, "cudaSetDevice");
     e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
     if (e != cudaSuccess) return fail(e, "cudaDeviceGetAttribute");
+    e = fill_prepare();
+    if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute");
     if (o.stream) {
         ctx->stream = (cudaStream_t)o.stream;
     } else {
@@ -1013,7 +1054,7 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
         if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune timing");
         return clue_sync(ctx);
     };
-    const float scales[] = {0.5f, 0.75f, 1.0f, 1.5f, 2.0f, 3.0f, 4.0f, 6.0f};
+    const float scales[] = {0.5f, 0.75f, 1.0f, 1.5f, 2.0f, 3.0f, 4.0f, 6.0f, 8.0f, 12.0f};
     const int blocks[] = {128, 256};
     const float user_bin = ctx->opts.bin_size;
     const int user_block = ctx->opts.block_size;

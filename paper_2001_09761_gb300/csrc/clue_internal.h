@@ -10,6 +10,12 @@ namespace clue {
 // an event; tile t covers [tiles[t].start, tiles[t].start + tiles[t].len).
 constexpr int TILE = 1024;
 
+// Limits of the grid fill's two-level sort (beyond them the direct sort runs):
+// layers (a per-tile histogram in shared memory and a table of tiles x layers)
+// and cells per layer (counted in one CTA's shared memory).
+constexpr int SEG_MAX_LAYERS = 1024;
+constexpr int SEG_MAX_CELLS = 16384;
+
 // Cluster id of a follower whose id has not been passed down yet (frontier
 // expansion).
 constexpr int32_t PENDING = -2;
@@ -85,9 +91,18 @@ struct Buffers {
     int32_t *rank;       // [N] arrival rank of the hit in its cell (from the count)
     int32_t *count;      // [C] hits per cell (zeroed per run)
     int32_t *cell_start; // [C + 1]
-    float4 *rec;         // [N] by hit: x, y, w, local cell (int bits), for the
-                         //     ranking's gather; aliases hr
+    float4 *rec;         // [N] direct sort: by hit, x, y, w, local cell (int bits),
+                         //     for the gather; two-level sort: by position in the
+                         //     layer segments, x, y, w, id (int bits); aliases hr
     int32_t *perm;       // [N] hit ids grouped by cell, unordered within a cell
+                         //     (direct sort); ranks beyond the registers (two-level)
+    int32_t *seg_cnt;    // [nseg] hits per (event, layer) segment (two-level sort)
+    int32_t *seg_start;  // [nseg + 1] segment offsets
+    int32_t *tbase;      // [ntiles * L] a tile's run in each of its layer segments
+    unsigned short *cell16;  // [N] cell in the layer by layered position (two-level
+                             //     sort; aliases key)
+    int64_t nseg;        // events x layers, or 0: the direct sort
+    int32_t max_cells;   // most cells in one layer (the cell sort's shared memory)
     int32_t *tmp;        // [N] the second expansion frontier
     float4 *sp;          // [N] hits sorted by (cell, id): x, y, w, id (int bits)
     int32_t *lay_s;      // [N] layer in sorted order
@@ -123,6 +138,14 @@ struct LaunchCfg {
 // ---- launchers (each enqueues its kernel(s) on `s`; return cudaError_t) ----
 cudaError_t launch_fill_count(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_cells(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
+// The two-level sort (b.nseg > 0): layer count, segment scan, placement, cell
+// sort.  fill_prepare raises the cell sort's shared-memory limit on the
+// current device; call it once per device before the first launch.
+cudaError_t fill_prepare();
+cudaError_t launch_fill_layers(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_scan_segs(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
+cudaError_t launch_fill_place(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_fill_cells(const Buffers &b, const Params &p, int max_cells, cudaStream_t s);
 cudaError_t launch_fill_scatter(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);

@@ -2,14 +2,27 @@
 // bodies, which the kernels in k_grid.cu wrap.
 //
 // The paper pushes each hit into its bin with an atomic (conflict (i) of
-// Sec. 3).  Here the index is a counting sort: hits are counted per cell (the
-// count's atomic hands each hit its arrival rank), cell offsets come from a
-// prefix sum, hit ids are scattered into their cell's segment, and a gather
-// writes the sorted copy (x, y, w, id packed in one float4 per hit, one
-// 16-byte load per candidate), which makes every later neighbour scan a walk
-// over contiguous memory.  The order of hits inside a cell is the atomics'
-// arrival order; no result depends on it (the density is an exact sum, the
-// nearest-higher a lexicographic minimum).
+// Sec. 3).  Here the index is a counting sort into one array of hits sorted by
+// (event, layer, cell), (x, y, w, id) packed in one float4 per hit, one 16-byte
+// load per candidate, which makes every later neighbour scan a walk over
+// contiguous memory.  Two forms give the same layout:
+//
+//  * the two-level sort (every layer of the batch with at most SEG_MAX_CELLS
+//    cells, at most SEG_MAX_LAYERS layers): hits are first counted per
+//    (event, layer) segment with a per-tile histogram in shared memory (one
+//    global atomic per tile and layer, not one per hit), a prefix sum over the
+//    segments places them, and the records are moved into their segment; then
+//    one CTA per segment counts its hits per cell in shared memory, scans the
+//    counts and writes the cell offsets and the sorted records.  The atomics
+//    that rank hits inside a cell are shared-memory ones;
+//  * the direct sort (any grid): hits are counted per cell with global
+//    atomics (each returning the hit's arrival rank), a prefix sum over all
+//    cells gives the offsets, hit ids are scattered into their cell's segment
+//    and a gather writes the sorted records.
+//
+// The order of hits inside a cell is the atomics' arrival order in both; no
+// result depends on it (the density is an exact sum, the nearest-higher a
+// lexicographic minimum).
 #pragma once
 
 #include "scan.cuh"
@@ -72,6 +85,272 @@ __device__ __forceinline__ void fill_canon_stage(const Buffers &b) {
             b.sp[pos] = make_float4(r.x, r.y, r.z, __int_as_float(g));
             b.lay_s[pos] = __float_as_int(r.w) / ev_nbxy;
         }
+    }
+}
+
+// --- two-level sort -----------------------------------------------------------
+
+constexpr int FILL_THREADS = 256;      // block of the tile-wise stages (TILE / 4)
+constexpr int SEG_THREADS = 512;       // block of the per-segment stage
+constexpr int SEG_SMEM_HITS = 16384;   // segments up to this size are permuted in shared memory
+static_assert(TILE % FILL_THREADS == 0, "tile / block");
+static_assert(SEG_SMEM_HITS <= 65536, "16-bit indices");
+
+// Layer count: the tile's hits per layer in a shared histogram, then one
+// global atomic per tile and layer reserves the tile's run in its (event,
+// layer) segment: tbase[tile * L + layer] (written for the tile's layers
+// only).  Layers outside [0, L) flag the input error and are clamped, as in
+// the direct sort.  All of a thread's loads are issued before its atomics, so
+// their latencies overlap.  Needs FILL_THREADS threads and L ints of dynamic
+// shared memory.
+__device__ __forceinline__ void fill_layers_stage(const Buffers &b, const Params &p) {
+    extern __shared__ int s_hist[];
+    constexpr int PER = TILE / FILL_THREADS;
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+        const Tile tl = b.tiles[t];
+        for (int l = threadIdx.x; l < p.L; l += FILL_THREADS) s_hist[l] = 0;
+        int lay[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int k = threadIdx.x + u * FILL_THREADS;
+            lay[u] = k < tl.len ? b.layer[tl.start + k] : 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int k = threadIdx.x + u * FILL_THREADS;
+            if (k < tl.len) {
+                int l = lay[u];
+                if (l < 0 || l >= p.L) {
+                    atomicOr(&b.ctrl->err, ERRBIT_INPUT);
+                    l = min(max(l, 0), p.L - 1);
+                }
+                atomicAdd(&s_hist[l], 1);
+                if (!p.chase) b.fcount[tl.start + k] = 0;  // follower counters of the lists
+            }
+        }
+        __syncthreads();
+        const int64_t sbase = (int64_t)tl.event * p.L, tb = (int64_t)t * p.L;
+        for (int l = threadIdx.x; l < p.L; l += FILL_THREADS) {
+            const int h = s_hist[l];
+            if (h) b.tbase[tb + l] = atomicAdd(&b.seg_cnt[sbase + l], h);
+        }
+        __syncthreads();  // s_hist is reset for the next tile
+    }
+}
+
+// Exclusive scan, in place, of a[0..4 * n4) in shared memory (16-byte
+// aligned) by the whole CTA: each warp takes a contiguous chunk and walks it
+// 32 int4 at a time (lane j reads the j-th 16 bytes: no bank conflicts), each
+// lane scanning its four entries, with the warps' chunk sums scanned in `ws`
+// (>= 32 ints).  Ends with a barrier.
+__device__ __forceinline__ void smem_excl_scan4(int *a, int n4, int *ws) {
+    int4 *a4 = reinterpret_cast<int4 *>(a);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (((n4 + nw - 1) / nw) + 31) & ~31;
+    const int c0 = min(warp * per, n4), c1 = min(c0 + per, n4);
+    int sum = 0;
+    for (int c = c0 + lane; c < c1; c += 32) {
+        const int4 v = a4[c];
+        sum += (v.x + v.y) + (v.z + v.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL_MASK, sum, o);
+    if (lane == 0) ws[warp] = sum;
+    __syncthreads();
+    if (warp == 0) {
+        const int v = lane < nw ? ws[lane] : 0;
+        const int incl = warp_incl_scan(v);
+        if (lane < nw) ws[lane] = incl - v;
+    }
+    __syncthreads();
+    int run = ws[warp];
+    for (int base = c0; base < c1; base += 32) {
+        const int c = base + lane;
+        const int4 v = c < c1 ? a4[c] : make_int4(0, 0, 0, 0);
+        const int t = (v.x + v.y) + (v.z + v.w);
+        const int incl = warp_incl_scan(t);
+        const int ex = run + incl - t;
+        if (c < c1) a4[c] = make_int4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
+        run += __shfl_sync(FULL_MASK, incl, 31);
+    }
+    __syncthreads();
+}
+
+// Zero a[0..4 * n4) in shared memory (16-byte aligned), 16 bytes per store.
+__device__ __forceinline__ void smem_zero4(int *a, int n4) {
+    int4 *a4 = reinterpret_cast<int4 *>(a);
+    for (int c = threadIdx.x; c < n4; c += blockDim.x) a4[c] = make_int4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ int cell_in_layer(float x, float y, const EventDesc &ev) {
+    return axis_bin(y, ev.ymin, ev.inv_s, ev.nby) * ev.nbx + axis_bin(x, ev.xmin, ev.inv_s, ev.nbx);
+}
+
+// Layer placement, one tile at a time: the tile's records are first sorted by
+// layer in shared memory (ranks from shared atomics), then written out so that
+// consecutive threads write consecutive slots of a layer's run, at the run
+// the count reserved, each with its cell in the layer (16 bits, in `cell16`).
+// The layer is clamped exactly as the count clamped it.  Needs FILL_THREADS
+// threads and L ints (rounded up to a multiple of 4) of dynamic shared memory.
+__device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params &p) {
+    __shared__ float4 s_rec[TILE];
+    __shared__ int s_lay[TILE];
+    __shared__ int ws[32];
+    extern __shared__ int4 s_off4[];  // tile offsets by layer, then destinations
+    int *s_off = reinterpret_cast<int *>(s_off4);
+    constexpr int PER = TILE / FILL_THREADS;
+    const int L4 = (p.L + 3) / 4;
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+        const Tile tl = b.tiles[t];
+        smem_zero4(s_off, L4);
+        float4 r[PER];
+        int lay[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int k = threadIdx.x + u * FILL_THREADS;
+            const int g = tl.start + (k < tl.len ? k : 0);
+            r[u] = make_float4(b.x[g], b.y[g], b.w[g], __int_as_float(g));
+            lay[u] = b.layer[g];
+        }
+        __syncthreads();
+        int rk[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int k = threadIdx.x + u * FILL_THREADS;
+            if (k < tl.len) {
+                if (!isfinite(r[u].x) || !isfinite(r[u].y) || !isfinite(r[u].z))
+                    atomicOr(&b.ctrl->err, ERRBIT_INPUT);
+                lay[u] = min(max(lay[u], 0), p.L - 1);
+                rk[u] = atomicAdd(&s_off[lay[u]], 1);
+            }
+        }
+        __syncthreads();
+        smem_excl_scan4(s_off, L4, ws);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int k = threadIdx.x + u * FILL_THREADS;
+            if (k < tl.len) {
+                const int slot = s_off[lay[u]] + rk[u];
+                s_rec[slot] = r[u];
+                s_lay[slot] = lay[u];
+            }
+        }
+        __syncthreads();
+        // slot i of layer l goes to dst[l] + i (only the tile's layers are read)
+        const int64_t sbase = (int64_t)tl.event * p.L, tb = (int64_t)t * p.L;
+        for (int i = threadIdx.x; i < tl.len; i += FILL_THREADS) {
+            const int l = s_lay[i];
+            if (i == 0 || s_lay[i - 1] != l)  // first slot of the layer's run
+                s_off[l] = b.seg_start[sbase + l] + b.tbase[tb + l] - s_off[l];
+        }
+        __syncthreads();
+        const EventDesc ev = b.events[tl.event];
+        for (int i = threadIdx.x; i < tl.len; i += FILL_THREADS) {
+            const float4 r = s_rec[i];
+            const int dst = s_off[s_lay[i]] + i;
+            b.rec[dst] = r;
+            b.cell16[dst] = (unsigned short)cell_in_layer(r.x, r.y, ev);
+        }
+        __syncthreads();  // the staging arrays are reused by the next tile
+    }
+}
+
+// L2 prefetch of `bytes` bytes at `p` (both multiples of 16) by the copy
+// engine: one instruction, no registers, no wait.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Cell sort of one segment per CTA.  The segment's records are first
+// prefetched into L2 (they are read once more, in sorted order, at the end).
+// Its hits are counted per cell in shared memory (cells from `cell16`), the
+// counts scanned and the layer's cell offsets written.  A segment of at most
+// SEG_SMEM_HITS hits is then permuted in shared memory: each hit, with its
+// cell still in registers (two 16-bit cells per register), takes its slot
+// with a shared atomic on its cell's running offset and stores its 16-bit
+// index there; the records are then written in slot order, a gather from L2
+// and coalesced stores.  A longer segment keeps the first pass's ranks in
+// `perm` and writes each record at its cell's offset plus its rank.  The last
+// segment also writes the end offset cell_start[C].  Needs SEG_THREADS
+// threads, and nbx * nby ints (rounded up to a multiple of 4) plus
+// SEG_SMEM_HITS 16-bit indices of dynamic shared memory.
+__device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params &p) {
+    extern __shared__ int4 s_cell4[];
+    __shared__ int ws[32];
+    int *s_cell = reinterpret_cast<int *>(s_cell4);
+    unsigned short *s_perm = (unsigned short *)(s_cell4 + (b.max_cells + 3) / 4);
+    constexpr int PER = SEG_SMEM_HITS / SEG_THREADS;  // hits per thread, small segments
+    constexpr unsigned NONE = 0xffffu;                 // no hit (cells are < 2^14)
+    constexpr int G = 4;                               // gathers in flight per thread
+    static_assert(PER % 2 == 0 && SEG_MAX_CELLS < (int)NONE, "cell packing");
+    for (int64_t sg = blockIdx.x; sg < b.nseg; sg += gridDim.x) {
+        const int e = (int)(sg / p.L);
+        const int l = (int)(sg - (int64_t)e * p.L);
+        const int nbxy = b.events[e].nbx * b.events[e].nby, n4 = (nbxy + 3) / 4;
+        const int64_t cbase = b.events[e].cell_off + (int64_t)l * nbxy;
+        const int s0 = b.seg_start[sg], n = b.seg_start[sg + 1] - s0;
+        const bool small = n <= SEG_SMEM_HITS;  // uniform over the CTA
+        if (small && n > 0 && threadIdx.x == 0) prefetch_l2_bulk(b.rec + s0, (unsigned)n * 16u);
+        const unsigned short *cell = b.cell16 + s0;
+        smem_zero4(s_cell, n4);
+        // this thread's hits: threadIdx.x + u * SEG_THREADS for u < mine
+        const int mine = n > (int)threadIdx.x ? (n - (int)threadIdx.x + SEG_THREADS - 1) / SEG_THREADS : 0;
+        unsigned cp[PER / 2];  // their cells, two per word
+        if (small) {
+#pragma unroll
+            for (int u = 0; u < PER; u += 2) {
+                if (u >= mine) break;
+                const int k = threadIdx.x + u * SEG_THREADS;
+                cp[u / 2] = cell[k] | (u + 1 < mine ? (unsigned)cell[k + SEG_THREADS] : NONE) << 16;
+            }
+        }
+        __syncthreads();
+        if (small) {
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                if (u >= mine) break;
+                atomicAdd(&s_cell[(cp[u / 2] >> (16 * (u & 1))) & 0xffffu], 1);
+            }
+        } else {
+            for (int k = threadIdx.x; k < n; k += SEG_THREADS)
+                b.perm[s0 + k] = atomicAdd(&s_cell[cell[k]], 1);
+        }
+        __syncthreads();
+        smem_excl_scan4(s_cell, n4, ws);
+        for (int c = threadIdx.x; c < nbxy; c += SEG_THREADS) b.cell_start[cbase + c] = s0 + s_cell[c];
+        if (sg == b.nseg - 1 && threadIdx.x == 0) b.cell_start[b.C] = s0 + n;
+        if (small) {
+            __syncthreads();  // the offsets are read before they become cursors
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                if (u >= mine) break;
+                const unsigned c = (cp[u / 2] >> (16 * (u & 1))) & 0xffffu;
+                s_perm[atomicAdd(&s_cell[c], 1)] = (unsigned short)(threadIdx.x + u * SEG_THREADS);
+            }
+            __syncthreads();
+            const float4 *rec = b.rec + s0;
+            float4 *sp = b.sp + s0;
+            int32_t *lay = b.lay_s + s0;
+            for (int u0 = 0; u0 < mine; u0 += G) {
+                float4 v[G];
+#pragma unroll
+                for (int u = 0; u < G; ++u)
+                    if (u0 + u < mine) v[u] = rec[s_perm[threadIdx.x + (u0 + u) * SEG_THREADS]];
+#pragma unroll
+                for (int u = 0; u < G; ++u)
+                    if (u0 + u < mine) {
+                        const int q = threadIdx.x + (u0 + u) * SEG_THREADS;
+                        sp[q] = v[u];
+                        lay[q] = l;
+                    }
+            }
+        } else {
+            for (int k = threadIdx.x; k < n; k += SEG_THREADS)
+                b.sp[s0 + s_cell[cell[k]] + b.perm[s0 + k]] = b.rec[s0 + k];
+            for (int k = threadIdx.x; k < n; k += SEG_THREADS) b.lay_s[s0 + k] = l;
+        }
+        __syncthreads();  // the shared arrays are reset for the next segment
     }
 }
 

@@ -1,5 +1,6 @@
 // Step S1: the fixed-grid spatial index (Sec. 2.1, Eqs. 1-2) as per-stage
-// kernels; the stage bodies and their description are in grid_stages.cuh.
+// kernels, both sorts; the stage bodies and their description are in
+// grid_stages.cuh.
 #include "grid_stages.cuh"
 
 namespace clue {
@@ -30,6 +31,55 @@ __global__ void __launch_bounds__(256) k_fill_canon(Buffers b) { fill_canon_stag
 cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
     const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
     k_fill_canon<<<grid > 0 ? grid : 1, c.block_fill, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+// The two tile-wise stages run one CTA per tile: a tile's steps are separated
+// by barriers, and many resident CTAs hide each other's latencies.
+__global__ void __launch_bounds__(FILL_THREADS) k_fill_layers(Buffers b, Params p) {
+    fill_layers_stage(b, p);
+}
+
+cudaError_t launch_fill_layers(const Buffers &b, const Params &p, const LaunchCfg &, cudaStream_t s) {
+    if (p.L < 1 || p.L > SEG_MAX_LAYERS) return cudaErrorInvalidValue;
+    const int grid = b.ntiles;
+    k_fill_layers<<<grid > 0 ? grid : 1, FILL_THREADS, (size_t)p.L * 4, s>>>(b, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_segs(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches) {
+    return exclusive_scan<int32_t>(LoadI32{b.seg_cnt}, b.nseg, b.seg_start,
+                                   (int32_t *)b.scan_partials, c.grid_cap, s, launches);
+}
+
+__global__ void __launch_bounds__(FILL_THREADS, 5) k_fill_place(Buffers b, Params p) {
+    fill_place_stage(b, p);
+}
+
+cudaError_t launch_fill_place(const Buffers &b, const Params &p, const LaunchCfg &, cudaStream_t s) {
+    if (p.L < 1 || p.L > SEG_MAX_LAYERS) return cudaErrorInvalidValue;
+    const int grid = b.ntiles;
+    k_fill_place<<<grid > 0 ? grid : 1, FILL_THREADS, (size_t)(p.L + 3) / 4 * 16, s>>>(b, p);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(SEG_THREADS, 2) k_fill_cells(Buffers b, Params p) {
+    fill_cells_stage(b, p);
+}
+
+constexpr int fill_cells_smem(int max_cells) { return (max_cells + 3) / 4 * 16 + SEG_SMEM_HITS * 2; }
+
+cudaError_t fill_prepare() {
+    return cudaFuncSetAttribute(k_fill_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                fill_cells_smem(SEG_MAX_CELLS));
+}
+
+// One CTA per segment (a grid-stride loop past 2^30 segments).
+cudaError_t launch_fill_cells(const Buffers &b, const Params &p, int max_cells, cudaStream_t s) {
+    if (max_cells < 1 || max_cells > SEG_MAX_CELLS || max_cells != b.max_cells || b.nseg < 1)
+        return cudaErrorInvalidValue;
+    const int64_t grid = b.nseg < (1 << 30) ? b.nseg : (1 << 30);
+    k_fill_cells<<<(unsigned)grid, SEG_THREADS, (size_t)fill_cells_smem(max_cells), s>>>(b, p);
     return cudaGetLastError();
 }
 

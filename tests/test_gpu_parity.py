@@ -207,7 +207,7 @@ def test_profiled_graph_replay_keeps_each_runs_times(clue_mod):
         cl.run_batch(tx, ty, tl, te, offs, gen.PARAMS_BLOBS, out=(cid, seed))
         if r >= 1:
             prev = cl.kernel_times(back=1)  # read while run r is queued
-            assert {"fill_count", "rho", "nh_delta", "assign"} <= set(prev)
+            assert {"fill_cells", "rho", "nh_delta", "assign"} <= set(prev)
     times = [cl.kernel_times(back=k) for k in range(4)]
     for t in times:
         assert set(t) == set(times[0]) and all(v >= 0 for v in t.values())
@@ -402,6 +402,38 @@ def test_dense_cells_and_exact_ties(clue_mod):
     assert_parity(_gpu_all(cl, ev, p), oracle.run_event(ev, p, 1, extent=ext))
 
 
+@pytest.mark.parametrize("form", ["two_level", "fine_grid", "many_layers", "long_segment"])
+def test_grid_fill_forms(clue_mod, form):
+    """Both forms of the grid fill, bit-exact against the oracle: the two-level
+    sort, the direct sort that a layer of more than 16384 cells or more than
+    1024 layers falls back to, and a 30000-hit layer segment (longer than the
+    two-level sort permutes in shared memory).  The profiled kernel names show which ran."""
+    ext = (-100.0, 100.0, -100.0, 100.0)
+    rng = np.random.default_rng(71)
+    kw, L = {}, 8
+    if form == "long_segment":
+        L = 1
+        ev = gen.make_event(30_000, 1, 72, "blobs", extent=ext)
+    elif form == "many_layers":
+        L = 5000
+        n = 20_000
+        ev = Ev(rng.uniform(-100, 100, n), rng.uniform(-100, 100, n),
+                rng.integers(0, L, n), rng.exponential(1.0, n))
+    elif form == "fine_grid":  # bins of d_c over 500 x 500: ~40000 cells per layer
+        ext = (-250.0, 250.0, -250.0, 250.0)
+        ev = gen.make_event(20_000, L, 73, "blobs", extent=ext)
+        kw = dict(bin_size=2.0)
+    else:
+        ev = gen.make_event(20_000, L, 73, "blobs", extent=ext)
+    cl = _cl(clue_mod, ext, L, **kw)
+    cl.set_profiling(True)
+    assert_parity(_gpu_all(cl, ev, gen.PARAMS_BLOBS),
+                  oracle.run_event(ev, gen.PARAMS_BLOBS, L, extent=ext))
+    direct = form in ("fine_grid", "many_layers")
+    names = set(cl.kernel_times())
+    assert ("fill_count" in names) == direct and ("fill_cells" in names) == (not direct)
+
+
 @pytest.mark.parametrize("expand", [0, 1], ids=["frontier", "chase"])
 def test_wide_tree_one_node_with_many_followers(clue_mod, expand):
     """2000 hits on a circle of radius 3 around one heavy hit.  They are
@@ -496,8 +528,9 @@ def test_stage_times_and_launch_count(clue_mod):
         assert list(st) == ["grid_fill", "rho", "nh_delta", "decide_followers", "expand"]
         assert all(v >= 0 for v in st.values())
         kt = cl.kernel_times()
-        assert {"fill_count", "rho", "nh_delta"} | last <= set(kt)
-        assert cl.launch_count() == (13 + 12 if expand == 0 else 10)  # one-CTA seed-rank scan
+        assert {"fill_cells", "rho", "nh_delta"} | last <= set(kt)
+        # two-level grid fill with a one-CTA segment scan (4); chase: one-CTA seed-rank scan
+        assert cl.launch_count() == (4 + 19 if expand == 0 else 8)
 
 
 def test_paper_parameter_workload(clue_mod):
@@ -544,7 +577,7 @@ def test_scratch_limit_fails_cleanly_then_recovers(clue_mod):
     allocation; the context stays usable for runs that fit."""
     small = gen.make_event(2000, 4, 1, "blobs")
     big = gen.make_event(400_000, 100, 2, "blobs")
-    cl = _cl(clue_mod, gen.EXTENT, 100, max_scratch_bytes=40_000_000)
+    cl = _cl(clue_mod, gen.EXTENT, 100, max_scratch_bytes=20_000_000)
     cid, _ = cl.run(small.x, small.y, small.layer, small.energy, gen.PARAMS_BLOBS)
     cl.sync()
     with pytest.raises(clue_mod.ClueError) as ei:
