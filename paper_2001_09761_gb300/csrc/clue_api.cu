@@ -228,8 +228,8 @@ int build_plan(clue_ctx *ctx, const int64_t *offsets, int32_t E, float dc, Plan 
 // Carve the scratch arrays of a run out of the arena; grows the arena
 // (after draining the stream) when it is too small.  With `dry` set only the
 // size is computed.
-size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t nseg, int64_t ntb,
-             bool dry) {
+size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t E, int64_t nseg,
+             int64_t ntb, bool dry) {
     size_t off = 0;
     char *base = ctx->arena;
     auto take = [&](size_t bytes) -> void * {
@@ -262,6 +262,7 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t nseg, int6
     b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
     b.front_a = b.perm;  // the frontiers reuse the grid fill's scratch
     b.front_b = b.tmp;
+    b.sid = b.tmp;  // the sorted ids are dead once rho has copied them
     const int64_t parts = std::max(scan_partials_needed(N), scan_partials_needed(C)) + 1;
     b.scan_partials = take((size_t)parts * 8);
     b.scan_partials_cap = parts;
@@ -269,6 +270,7 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t nseg, int6
     b.seg_cnt = nseg ? (int32_t *)take((size_t)nseg * 4) : nullptr;
     b.seg_start = nseg ? (int32_t *)take((size_t)(nseg + 1) * 4) : nullptr;
     b.tbase = ntb ? (int32_t *)take((size_t)ntb * 4) : nullptr;
+    b.wexp = (uint32_t *)take((size_t)E * 8);
     return off;
 }
 
@@ -388,6 +390,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     else
         CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
     if (p.chase) CK(cudaMemsetAsync(b.sbits, 0, (size_t)(b.N / 32 + 1) * 4, s));
+    CK(cudaMemsetAsync(b.wexp, 0xff, (size_t)b.nevents * 8, s));
     CK(rec(nullptr));
     if (b.nseg) {  // two-level sort: layer segments, then cells
         CK(launch_fill_layers(b, p, cfg, s));
@@ -405,7 +408,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
         CK(rec("scan_cells"));
         CK(launch_fill_scatter(b, cfg, s));
         CK(rec("fill_scatter"));
-        CK(launch_fill_canon(b, cfg, s));
+        CK(launch_fill_canon(b, p, cfg, s));
         CK(rec("fill_canon"));
     }
     nl += 3;
@@ -569,10 +572,11 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     rc = build_plan(ctx, offsets, E, dc, plan);
     if (rc) return rc;
     Buffers b{};
-    const size_t need = carve(ctx, b, plan.N, plan.C, plan.nseg, plan.ntb, true);
+    const int64_t E64 = (int64_t)plan.ev.size();
+    const size_t need = carve(ctx, b, plan.N, plan.C, E64, plan.nseg, plan.ntb, true);
     rc = ensure_arena(ctx, need);
     if (rc) return rc;
-    carve(ctx, b, plan.N, plan.C, plan.nseg, plan.ntb, false);
+    carve(ctx, b, plan.N, plan.C, E64, plan.nseg, plan.ntb, false);
     b.x = x;
     b.y = y;
     b.w = energy;

@@ -99,12 +99,19 @@ struct Buffers {
     int32_t *seg_cnt;    // [nseg] hits per (event, layer) segment (two-level sort)
     int32_t *seg_start;  // [nseg + 1] segment offsets
     int32_t *tbase;      // [ntiles * L] a tile's run in each of its layer segments
+    uint32_t *wexp;      // [2 * nevents] weight range of each event, from the fill:
+                         //     min over its finite nonzero weights of max(biased
+                         //     exponent, 1), and min of 255 - biased exponent
+                         //     (0xffffffff: none; set to all ones per run)
     unsigned short *cell16;  // [N] cell in the layer by layered position (two-level
                              //     sort; aliases key)
     int64_t nseg;        // events x layers, or 0: the direct sort
     int32_t max_cells;   // most cells in one layer (the cell sort's shared memory)
     int32_t *tmp;        // [N] the second expansion frontier
-    float4 *sp;          // [N] hits sorted by (cell, id): x, y, w, id (int bits)
+    float4 *sp;          // [N] hits sorted by cell: x, y, w, id (int bits), or for an
+                         //     event on the flat kernel's fixed point x, y and the
+                         //     64-bit integer weight (two words)
+    int32_t *sid;        // [N] hit id by sorted position (aliases tmp)
     int32_t *lay_s;      // [N] layer in sorted order
     // density
     float4 *spr;         // [N] sorted order: x, y, rho, id (written by the rho step)
@@ -147,7 +154,7 @@ cudaError_t launch_scan_segs(const Buffers &b, const LaunchCfg &c, cudaStream_t 
 cudaError_t launch_fill_place(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_fill_cells(const Buffers &b, const Params &p, int max_cells, cudaStream_t s);
 cudaError_t launch_fill_scatter(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_fill_canon(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s,

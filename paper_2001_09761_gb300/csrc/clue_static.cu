@@ -41,7 +41,7 @@ constexpr size_t STATIC_BYTES =
     al(NB * 16) /*sp*/ + al(NB * 4) /*lay_s*/ +
     al(NB * 16) /*rec = hr*/ + al(NB * 16) /*spr*/ +
     al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
-    al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/;
+    al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/ + al(8) /*wexp*/;
 
 }  // namespace
 
@@ -150,8 +150,10 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
     b.front_a = b.perm;
     b.front_b = b.tmp;
+    b.sid = b.tmp;
     b.scan_partials = take((size_t)STATIC_PARTS * 8);
     b.scan_partials_cap = STATIC_PARTS;
+    b.wexp = (uint32_t *)take(8);
     if ((size_t)(p - (char *)base) > STATIC_BYTES) return CLUE_ERR_STATE;
 
     // The plan of one event: its descriptor and its tiles.
@@ -218,11 +220,12 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     SCK(cudaMemcpyAsync(d_tiles, host.tiles, ntiles * sizeof(Tile), cudaMemcpyHostToDevice, s));
     SCK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
     SCK(cudaMemsetAsync(b.count, 0, (size_t)C * 4, s));
+    SCK(cudaMemsetAsync(b.wexp, 0xff, 8, s));
     int nl = 0;
     SCK(launch_fill_count(b, prm, cfg, s));
     SCK(launch_scan_cells(b, cfg, s, &nl));
     SCK(launch_fill_scatter(b, cfg, s));
-    SCK(launch_fill_canon(b, cfg, s));
+    SCK(launch_fill_canon(b, prm, cfg, s));
     SCK(launch_rho(b, prm, cfg, s));
     SCK(launch_nh(b, prm, cfg, s));
     SCK(launch_scan_hits(b, prm, cfg, s, &nl));

@@ -17,7 +17,12 @@
 // and proves c exact from the smallest term and the largest |s| (below);
 // then s + c is the exact sum and one fp32 addition rounds it correctly.
 // When the proof fails (terms over more than ~24 binary orders of magnitude,
-// or an overflow) an integer accumulator recomputes the sum exactly.
+// or an overflow) an integer accumulator recomputes the sum exactly.  With
+// the flat chi the terms are the weights themselves, and an event whose
+// weights span few enough binary orders (the fill records each event's
+// exponent range) is summed in 64-bit fixed point instead: every weight is an
+// integer multiple of the event's smallest weight's last place, so the sum is
+// an exact integer, rounded once at the end (rho_stage below).
 #pragma once
 
 #include <climits>
@@ -124,9 +129,11 @@ __device__ __forceinline__ float term_of(float d2, float w, float inv) {
 }
 
 // rho by the integer accumulator: the rare windows the fast path cannot prove.
+// `unit` is nonzero when the records hold fixed-point weights (flat kernel),
+// whose weight is then iw * unit, exactly.
 template <int CHI>
 __device__ __noinline__ float rho_wide(const Buffers &b, int64_t plane, int nbx, Window w,
-                                       float xi, float yi, float dc2, float inv) {
+                                       float xi, float yi, float dc2, float inv, float unit) {
     Wide acc{{0ull, 0ull, 0ull, 0ull, 0ull}};
     for (int by = w.ly; by <= w.hy; ++by) {
         const int64_t row = plane + (int64_t)by * nbx;
@@ -134,7 +141,8 @@ __device__ __noinline__ float rho_wide(const Buffers &b, int64_t plane, int nbx,
         for (int u = b.cell_start[row + w.lx]; u < e; ++u) {
             const float4 h = b.sp[u];
             const float d2 = sq_dist(xi, yi, h.x, h.y);
-            if (d2 < dc2) wide_add(acc, term_of<CHI>(d2, h.z, inv));
+            const float wj = unit != 0.0f ? __fmul_rn(__ll2float_rn(fixed_weight_of(h)), unit) : h.z;
+            if (d2 < dc2) wide_add(acc, term_of<CHI>(d2, wj, inv));
         }
     }
     return wide_round(acc);
@@ -148,6 +156,18 @@ __device__ __noinline__ float rho_wide(const Buffers &b, int64_t plane, int nbx,
 // is a multiple of 2^(g - 150) below 2^(L + E - 151) <= 2^(g - 126) when
 // L + E - 25 <= g: at most 24 significant bits, so an fp32 value, and
 // c = fl(c + e_k) never rounds.  Then s + c is the exact sum.
+//
+// The fixed-point path (flat chi).  Let g be the event's smallest max(biased
+// exponent, 1) over its nonzero weights and E its largest biased exponent.
+// Every weight is mant 2^(max(e, 1) - 150) with mant < 2^24, so w 2^(150 - g)
+// is an integer below 2^(24 + E - g): the scaling by a power of two and the
+// conversion to a 64-bit integer are exact.  A window of T candidates sums
+// fewer than T such integers, below 2^63 when 24 + E - g + bitlen(T) <= 63,
+// so the 64-bit sum is exact.  Its conversion to fp32 rounds once (to
+// nearest, ties to even) and the scaling back by 2^(g - 150) is exact while
+// the result is normal, which g >= 24 ensures (a nonzero sum is at least
+// 2^(g - 150)); an overflow gives inf as the correctly rounded sum would.
+// Windows past the bound go to the integer accumulator.
 template <int CHI>
 __device__ __forceinline__ void rho_stage(const Buffers &b, const Params &p) {
     const float4 *__restrict__ sp = b.sp;
@@ -155,6 +175,34 @@ __device__ __forceinline__ void rho_stage(const Buffers &b, const Params &p) {
         const Tile tl = b.tiles[t];
         const EventDesc ev = b.events[tl.event];
         const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
+        // the fill stored this event's records in fixed point or not (uniform)
+        const FixedW fw = fixed_weights(b.wexp + 2 * tl.event, CHI);
+        if (CHI == 0 && fw.on) {
+            for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+                const int q = tl.start + k;
+                const float4 me = sp[q];
+                const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
+                const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
+                long long acc = 0;
+                unsigned T = 0;
+                for (int by = w.ly; by <= w.hy; ++by) {
+                    const int64_t row = plane + (int64_t)by * ev.nbx;
+                    const int u0 = b.cell_start[row + w.lx], e = b.cell_start[row + w.hx + 1];
+                    T += (unsigned)(e - u0);
+                    for (int u = u0; u < e; ++u) {  // branch-free body
+                        const float4 h = sp[u];
+                        const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                        acc += d2 < p.dc2 ? fixed_weight_of(h) : 0ll;
+                    }
+                }
+                const float r = 32 - __clz(T) <= fw.budget
+                                    ? __fmul_rn(__ll2float_rn(acc), fw.unit)
+                                    : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv,
+                                                    fw.unit);
+                b.spr[q] = make_float4(me.x, me.y, r, __int_as_float(b.sid[q]));  // for the nh step
+            }
+            continue;
+        }
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
             const float4 me = sp[q];
@@ -188,8 +236,9 @@ __device__ __forceinline__ void rho_stage(const Buffers &b, const Params &p) {
             const int L = 32 - __clz(m);
             const bool exact = E < 255 && L + E - 25 <= g;
             const float r = exact ? __fadd_rn(s, c)
-                                  : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv);
-            b.spr[q] = make_float4(me.x, me.y, r, me.w);  // x, y, rho, id for the nh step
+                                  : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv,
+                                                  0.0f);
+            b.spr[q] = make_float4(me.x, me.y, r, __int_as_float(b.sid[q]));  // for the nh step
         }
     }
 }

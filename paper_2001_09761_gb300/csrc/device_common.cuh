@@ -13,6 +13,63 @@ constexpr unsigned FULL_MASK = 0xffffffffu;
 
 // Squared distance in fp32, every operation rounded on its own (no FMA):
 // dx = xj - xi, dy = yj - yi, dx*dx + dy*dy.  It is exactly symmetric in i, j.
+// An event's weight range: [0] the min of max(biased exponent, 1), [1] the
+// min of 255 - biased exponent, over its finite nonzero weights (all ones:
+// none yet).  A CTA gathers its tile's range in shared memory: a warp-wide
+// minimum, one shared atomic per warp (every lane of the warp calls it;
+// `active` lanes contribute w) ...
+__device__ __forceinline__ void weight_range_add(unsigned *s_w, float w, bool active) {
+    const unsigned bits = __float_as_uint(w) & 0x7fffffffu;
+    const unsigned eb = bits >> 23;
+    const bool nz = active && bits != 0u && eb < 255u;
+    const unsigned lo = __reduce_min_sync(FULL_MASK, nz ? max(eb, 1u) : 0xffffffffu);
+    const unsigned hi = __reduce_min_sync(FULL_MASK, nz ? 255u - eb : 0xffffffffu);
+    if ((threadIdx.x & 31) == 0 && lo != 0xffffffffu) {
+        atomicMin(&s_w[0], lo);
+        atomicMin(&s_w[1], hi);
+    }
+}
+
+// ... and one thread folds it into the event's after a barrier, with an atomic
+// only where it lowers the value held (which only falls, so a stale read
+// costs at most a redundant atomic).
+__device__ __forceinline__ void weight_range_flush(uint32_t *wexp_e, const unsigned *s_w) {
+    if (s_w[0] < __ldcg(&wexp_e[0])) atomicMin(&wexp_e[0], s_w[0]);
+    if (s_w[1] < __ldcg(&wexp_e[1])) atomicMin(&wexp_e[1], s_w[1]);
+}
+
+// The flat kernel's 64-bit fixed point for one event (see rho_stage): on when
+// the event's weights span few enough binary orders; scale = 2^(150 - g)
+// turns a weight into an exact integer, unit = 2^(g - 150) turns it back, and
+// a window of T candidates is exact while bitlen(T) <= budget.
+struct FixedW {
+    bool on;
+    float scale, unit;
+    int budget;
+};
+
+__device__ __forceinline__ FixedW fixed_weights(const uint32_t *wexp_e, int chi) {
+    const unsigned g = wexp_e[0], e = 255u - wexp_e[1];
+    FixedW f;
+    f.on = chi == 0 && g >= 24u && g <= 254u && e >= g && 25u + (e - g) <= 63u;
+    f.scale = f.on ? __uint_as_float((277u - g) << 23) : 0.0f;
+    f.unit = f.on ? __uint_as_float((g - 23u) << 23) : 0.0f;
+    f.budget = f.on ? 39 - (int)(e - g) : 0;
+    return f;
+}
+
+// The sorted record of a hit: (x, y, w, id), or under the fixed point
+// (x, y, low and high words of the integer weight w 2^(150 - g)).
+__device__ __forceinline__ float4 sorted_record(const float4 &r, const FixedW &f) {
+    if (!f.on) return r;
+    const long long iw = __float2ll_rz(__fmul_rn(r.z, f.scale));
+    return make_float4(r.x, r.y, __int_as_float((int)(unsigned)iw), __int_as_float((int)(iw >> 32)));
+}
+
+__device__ __forceinline__ long long fixed_weight_of(const float4 &h) {
+    return (long long)(((unsigned long long)__float_as_uint(h.w) << 32) | __float_as_uint(h.z));
+}
+
 __device__ __forceinline__ float sq_dist(float xi, float yi, float xj, float yj) {
     const float dx = __fsub_rn(xj, xi);
     const float dy = __fsub_rn(yj, yi);

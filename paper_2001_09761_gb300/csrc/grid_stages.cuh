@@ -31,10 +31,16 @@ namespace clue {
 
 // --- count: bin of every hit, hits per cell ---------------------------------
 __device__ __forceinline__ void fill_count_stage(const Buffers &b, const Params &p) {
+    __shared__ unsigned s_w[2];  // the tile's weight range
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const EventDesc ev = b.events[tl.event];
-        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+        if (threadIdx.x == 0) s_w[0] = s_w[1] = 0xffffffffu;
+        __syncthreads();
+        for (int k0 = 0; k0 < tl.len; k0 += blockDim.x) {  // uniform over the warp
+            const int k = k0 + threadIdx.x;
+            weight_range_add(s_w, b.w[tl.start + (k < tl.len ? k : 0)], k < tl.len);
+            if (k >= tl.len) continue;
             const int g = tl.start + k;
             const float x = b.x[g], y = b.y[g], w = b.w[g];
             int l = b.layer[g];
@@ -51,6 +57,8 @@ __device__ __forceinline__ void fill_count_stage(const Buffers &b, const Params 
             b.rec[g] = make_float4(x, y, w, __int_as_float(local));  // gathered by the ranking
             if (!p.chase) b.fcount[g] = 0;  // follower counters of the follower lists
         }
+        __syncthreads();
+        if (threadIdx.x == 0) weight_range_flush(b.wexp + 2 * tl.event, s_w);
     }
 }
 
@@ -74,15 +82,17 @@ __device__ __forceinline__ void fill_scatter_stage(const Buffers &b) {
 }
 
 // --- gather: the sorted copy of every hit, in the order of the segments ---
-__device__ __forceinline__ void fill_canon_stage(const Buffers &b) {
+__device__ __forceinline__ void fill_canon_stage(const Buffers &b, const Params &p) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int ev_nbxy = b.events[tl.event].nbx * b.events[tl.event].nby;
+        const FixedW fw = fixed_weights(b.wexp + 2 * tl.event, p.chi);
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int pos = tl.start + k;
             const int g = b.perm[pos];
             const float4 r = b.rec[g];  // x, y, w, cell of hit g: one 16-byte gather
-            b.sp[pos] = make_float4(r.x, r.y, r.z, __int_as_float(g));
+            b.sp[pos] = sorted_record(make_float4(r.x, r.y, r.z, __int_as_float(g)), fw);
+            b.sid[pos] = g;
             b.lay_s[pos] = __float_as_int(r.w) / ev_nbxy;
         }
     }
@@ -197,6 +207,7 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
     __shared__ float4 s_rec[TILE];
     __shared__ int s_lay[TILE];
     __shared__ int ws[32];
+    __shared__ unsigned s_w[2];  // the tile's weight range
     extern __shared__ int4 s_off4[];  // tile offsets by layer, then destinations
     int *s_off = reinterpret_cast<int *>(s_off4);
     constexpr int PER = TILE / FILL_THREADS;
@@ -204,6 +215,7 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         smem_zero4(s_off, L4);
+        if (threadIdx.x == 0) s_w[0] = s_w[1] = 0xffffffffu;
         float4 r[PER];
         int lay[PER];
 #pragma unroll
@@ -214,6 +226,9 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
             lay[u] = b.layer[g];
         }
         __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u)
+            weight_range_add(s_w, r[u].z, (int)threadIdx.x + u * FILL_THREADS < tl.len);
         int rk[PER];
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
@@ -227,6 +242,7 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
         }
         __syncthreads();
         smem_excl_scan4(s_off, L4, ws);
+        if (threadIdx.x == 0) weight_range_flush(b.wexp + 2 * tl.event, s_w);
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int k = threadIdx.x + u * FILL_THREADS;
@@ -291,6 +307,7 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
         const int64_t cbase = b.events[e].cell_off + (int64_t)l * nbxy;
         const int s0 = b.seg_start[sg], n = b.seg_start[sg + 1] - s0;
         const bool small = n <= SEG_SMEM_HITS;  // uniform over the CTA
+        const FixedW fw = fixed_weights(b.wexp + 2 * e, p.chi);
         if (small && n > 0 && threadIdx.x == 0) prefetch_l2_bulk(b.rec + s0, (unsigned)n * 16u);
         const unsigned short *cell = b.cell16 + s0;
         smem_zero4(s_cell, n4);
@@ -331,6 +348,7 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
             __syncthreads();
             const float4 *rec = b.rec + s0;
             float4 *sp = b.sp + s0;
+            int32_t *sid = b.sid + s0;
             int32_t *lay = b.lay_s + s0;
             for (int u0 = 0; u0 < mine; u0 += G) {
                 float4 v[G];
@@ -341,13 +359,18 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
                 for (int u = 0; u < G; ++u)
                     if (u0 + u < mine) {
                         const int q = threadIdx.x + (u0 + u) * SEG_THREADS;
-                        sp[q] = v[u];
+                        sp[q] = sorted_record(v[u], fw);
+                        sid[q] = __float_as_int(v[u].w);
                         lay[q] = l;
                     }
             }
         } else {
-            for (int k = threadIdx.x; k < n; k += SEG_THREADS)
-                b.sp[s0 + s_cell[cell[k]] + b.perm[s0 + k]] = b.rec[s0 + k];
+            for (int k = threadIdx.x; k < n; k += SEG_THREADS) {
+                const float4 r = b.rec[s0 + k];
+                const int q = s0 + s_cell[cell[k]] + b.perm[s0 + k];
+                b.sp[q] = sorted_record(r, fw);
+                b.sid[q] = __float_as_int(r.w);
+            }
             for (int k = threadIdx.x; k < n; k += SEG_THREADS) b.lay_s[s0 + k] = l;
         }
         __syncthreads();  // the shared arrays are reset for the next segment

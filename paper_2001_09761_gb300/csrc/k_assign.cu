@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) k_export(Buffers b, float *rho, float *de
         const int64_t hoff = b.events[tl.event].hit_off;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
-            const int g = __float_as_int(b.sp[q].w);
+            const int g = __float_as_int(b.spr[q].w);
             const float2 h = b.hr[q];
             if (rho) rho[g] = b.spr[q].z;
             if (delta) delta[g] = sqrtf(h.x);

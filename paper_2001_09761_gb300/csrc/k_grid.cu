@@ -26,11 +26,11 @@ cudaError_t launch_fill_scatter(const Buffers &b, const LaunchCfg &c, cudaStream
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_fill_canon(Buffers b) { fill_canon_stage(b); }
+__global__ void __launch_bounds__(256) k_fill_canon(Buffers b, Params p) { fill_canon_stage(b, p); }
 
-cudaError_t launch_fill_canon(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
+cudaError_t launch_fill_canon(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
     const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
-    k_fill_canon<<<grid > 0 ? grid : 1, c.block_fill, 0, s>>>(b);
+    k_fill_canon<<<grid > 0 ? grid : 1, c.block_fill, 0, s>>>(b, p);
     return cudaGetLastError();
 }
 

@@ -236,6 +236,27 @@ def test_exact_rho_with_adversarial_weights(clue_mod, chi, s):
                              chi_param=s))
 
 
+@pytest.mark.parametrize("span", [15, 36, 37, 38, 39])
+def test_fixed_point_rho_at_its_bounds(clue_mod, span):
+    """The flat kernel sums an event's weights in 64-bit fixed point when
+    24 + (exponent span) + bitlen(window candidates) <= 63.  Weights of both
+    signs span `span` binary orders (both ends present), in dense blobs so
+    windows hold dozens of candidates: span 15 takes the fixed point
+    everywhere, 36-38 leave it only a few candidate bits (most windows fall
+    back to the integer accumulator), 39 leaves the event on TwoSum.  Every
+    output is bit-exact against the oracle."""
+    ev = gen.make_event(20_000, 4, 78, "blobs")
+    rng = np.random.default_rng(span)
+    e = rng.integers(0, span + 1, ev.n)
+    e[:2] = (0, span)
+    w = np.ldexp(1.0 + rng.integers(0, 1 << 23, ev.n) / float(1 << 23), e - 20)
+    w = (w * np.where(rng.random(ev.n) < 0.2, -1.0, 1.0)).astype(np.float32)
+    cl = _cl(clue_mod, gen.EXTENT, 4)
+    ev2 = gen.Event(ev.x, ev.y, ev.layer, w)
+    assert_parity(_gpu_all(cl, ev2, gen.PARAMS_BLOBS),
+                  oracle.run(ev.x, ev.y, ev.layer, w, gen.PARAMS_BLOBS, 4))
+
+
 def test_exact_rho_of_coincident_sets(clue_mod):
     """Hits at one point are mutual neighbours, so rho is the rounded exact
     sum of the whole set: rounding up, to even, to a subnormal, to zero by
