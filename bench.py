@@ -171,9 +171,9 @@ def run_reference(args):
 # read once and every result written once (no re-reads, no scratch beyond
 # the stage's own outputs).
 ALG_BYTES = {
-    "fill_layers": 4 + 4,              # layer in; rank in the (event, layer) segment out
-    "fill_place": 16 + 4 + 16,         # x, y, w, layer, segment rank in; layered record out
-    "fill_cells": 16 + 16 + 4,         # layered record in; sorted record, layer out
+    "fill_layers": 4,                  # layer in (out: one int per tile and layer)
+    "fill_place": 16 + 16 + 2,         # x, y, w, layer in; layered record, 16-bit cell out
+    "fill_cells": 16 + 2 + 16 + 4 + 4,  # layered record, cell in; sorted record, layer, id out
     "fill_count": 16 + 4 + 4 + 4,      # x, y, w, layer in; cell, rank, cell count out
     "fill_scatter": 4 + 4 + 4 + 4,     # cell, rank, cell start in; hit id out
     "fill_canon": 4 + 16 + 16 + 4,     # id, packed record in; sorted hit, layer out
@@ -310,12 +310,12 @@ def served(torch, clue, tuning, dev, peak_mhits, args):
 
 
 def profile_case():
-    """The small case the ncu captures use: 10 scaling events (100 layers x
-    10k hits, seeds 0-9, 10M hits, inputs 160 MB > L2) clustered twice as one
+    """The small case the ncu captures use: the first 40 events of the
+    256-event batch (same size draw, 9.94M hits, inputs 159 MB > L2; the
+    batch's mix of event sizes and so of bin sizes), clustered twice as one
     batch with the default tuning and no graph; prints nothing else."""
     from paper_2001_09761_gb300 import clue
-    evs = [gen.scaling_event(10000, s) for s in range(10)]
-    x, y, l, e, offs = gen.concat(evs)
+    x, y, l, e, offs = gen.concat(make_workload(0, 40, 1e4, 1e6))
     cl = clue.Clusterer(extent=gen.EXTENT, max_layers=100, use_graphs=False)
     for _ in range(2):
         cl.run_batch(x, y, l, e, offs, PARAMS)
@@ -342,7 +342,7 @@ def main():
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--loads", type=float, nargs="*", default=[0.1, 0.5, 0.9])
     ap.add_argument("--profile-case", action="store_true",
-                    help="run the ncu case only: 10 events x 100 layers x 10k hits, twice")
+                    help="run the ncu case only: the batch's first 40 events, twice")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case()

@@ -42,18 +42,18 @@ __device__ __forceinline__ int seed_rank(const Buffers &b, int64_t g) {
     return b.sword[g >> 5] + __popc(b.sbits[g >> 5] & below);
 }
 
-// Seeds take their per-event id; seeds with followers enter the first
-// frontier of the expansion (one atomic per CTA); followers enter the CSR list
-// of their nearest-higher at the rank the decision step's count returned
-// (order inside a list is irrelevant: each follower has exactly one parent);
-// everything else is noise for now.
-__device__ __forceinline__ void link_stage(const Buffers &b, const Params &p) {
+// Frontier mode: seeds take their per-event id; seeds with followers enter
+// the first frontier of the expansion (one atomic per CTA); followers enter
+// the CSR list of their nearest-higher at the rank the decision step's count
+// returned (order inside a list is irrelevant: each follower has exactly one
+// parent); everything else is noise for now.
+__device__ __forceinline__ void link_stage(const Buffers &b, const Params &) {
     __shared__ int ws[32];
     __shared__ int s_base;
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int64_t hoff = b.events[tl.event].hit_off;
-        const unsigned ebase = p.chase ? (unsigned)seed_rank(b, hoff) : (unsigned)(b.hs[hoff] >> 32);
+        const unsigned ebase = (unsigned)(b.hs[hoff] >> 32);
         for (int k0 = 0; k0 < tl.len; k0 += blockDim.x) {
             const int k = k0 + threadIdx.x;
             int root = 0;
@@ -61,25 +61,20 @@ __device__ __forceinline__ void link_stage(const Buffers &b, const Params &p) {
                 const int g = tl.start + k;
                 const int code = b.code[g];
                 if (code == CODE_SEED) {
-                    if (p.chase) {
-                        b.cid[g] = (int32_t)((unsigned)seed_rank(b, g) - ebase);
-                    } else {
-                        const unsigned long long hg = b.hs[g];
-                        b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);
-                        root = (unsigned)b.hs[g + 1] != (unsigned)hg;  // has followers
-                    }
+                    const unsigned long long hg = b.hs[g];
+                    b.cid[g] = (int32_t)((unsigned)(hg >> 32) - ebase);
+                    root = (unsigned)b.hs[g + 1] != (unsigned)hg;  // has followers
                     b.is_seed[g] = 1;
                 } else {
                     b.is_seed[g] = 0;
                     if (code >= 0) {  // a follower of nh = code
-                        if (!p.chase) b.fol[(int)(unsigned)b.hs[code] + b.frank[g]] = g;
+                        b.fol[(int)(unsigned)b.hs[code] + b.frank[g]] = g;
                         b.cid[g] = PENDING;
                     } else {
                         b.cid[g] = -1;
                     }
                 }
             }
-            if (p.chase) continue;  // no expansion lists to fill
             int n_root;
             const int r = block_incl_scan(root, ws, &n_root) - root;
             if (n_root) {
