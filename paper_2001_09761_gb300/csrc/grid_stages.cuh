@@ -282,24 +282,24 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) 
 // prefetched into L2 (they are read once more, in sorted order, at the end).
 // Its hits are counted per cell in shared memory (cells from `cell16`), the
 // counts scanned and the layer's cell offsets written.  A segment of at most
-// SEG_SMEM_HITS hits is then permuted in shared memory: each hit, with its
-// cell still in registers (two 16-bit cells per register), takes its slot
-// with a shared atomic on its cell's running offset and stores its 16-bit
-// index there; the records are then written in slot order, a gather from L2
-// and coalesced stores.  A longer segment keeps the first pass's ranks in
-// `perm` and writes each record at its cell's offset plus its rank.  The last
-// segment also writes the end offset cell_start[C].  Needs SEG_THREADS
-// threads, and nbx * nby ints (rounded up to a multiple of 4) plus
-// SEG_SMEM_HITS 16-bit indices of dynamic shared memory.
+// SEG_SMEM_HITS hits is then permuted in shared memory: a second pass over
+// its cells (just read, so in L2) takes each hit's slot with a shared atomic
+// on its cell's running offset and stores the hit's 16-bit index there; the
+// records are then written in slot order, a gather from L2 and coalesced
+// stores.  A longer segment keeps the first pass's ranks in `perm` and writes
+// each record at its cell's offset plus its rank.  Loads are issued in
+// batches ahead of the atomics and stores that use them; the kernel keeps to
+// 42 registers so that three CTAs share an SM.  The last segment also writes
+// the end offset cell_start[C].  Needs SEG_THREADS threads, and nbx * nby ints
+// (rounded up to a multiple of 4) plus SEG_SMEM_HITS 16-bit indices of dynamic
+// shared memory.
 __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params &p) {
     extern __shared__ int4 s_cell4[];
     __shared__ int ws[32];
     int *s_cell = reinterpret_cast<int *>(s_cell4);
     unsigned short *s_perm = (unsigned short *)(s_cell4 + (b.max_cells + 3) / 4);
-    constexpr int PER = SEG_SMEM_HITS / SEG_THREADS;  // hits per thread, small segments
-    constexpr unsigned NONE = 0xffffu;                 // no hit (cells are < 2^14)
-    constexpr int G = 4;                               // gathers in flight per thread
-    static_assert(PER % 2 == 0 && SEG_MAX_CELLS < (int)NONE, "cell packing");
+    constexpr int C = 8;  // cells loaded per batch
+    constexpr int G = 2;  // gathers in flight per thread
     for (int64_t sg = blockIdx.x; sg < b.nseg; sg += gridDim.x) {
         const int e = (int)(sg / p.L);
         const int l = (int)(sg - (int64_t)e * p.L);
@@ -311,27 +311,20 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
         if (small && n > 0 && threadIdx.x == 0) prefetch_l2_bulk(b.rec + s0, (unsigned)n * 16u);
         const unsigned short *cell = b.cell16 + s0;
         smem_zero4(s_cell, n4);
-        // this thread's hits: threadIdx.x + u * SEG_THREADS for u < mine
-        const int mine = n > (int)threadIdx.x ? (n - (int)threadIdx.x + SEG_THREADS - 1) / SEG_THREADS : 0;
-        unsigned cp[PER / 2];  // their cells, two per word
-        if (small) {
-#pragma unroll
-            for (int u = 0; u < PER; u += 2) {
-                if (u >= mine) break;
-                const int k = threadIdx.x + u * SEG_THREADS;
-                cp[u / 2] = cell[k] | (u + 1 < mine ? (unsigned)cell[k + SEG_THREADS] : NONE) << 16;
-            }
-        }
         __syncthreads();
-        if (small) {
+        for (int k0 = threadIdx.x; k0 < n; k0 += C * SEG_THREADS) {
+            unsigned c[C];
 #pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                if (u >= mine) break;
-                atomicAdd(&s_cell[(cp[u / 2] >> (16 * (u & 1))) & 0xffffu], 1);
+            for (int u = 0; u < C; ++u) {
+                const int k = k0 + u * SEG_THREADS;
+                c[u] = k < n ? cell[k] : 0xffffu;
             }
-        } else {
-            for (int k = threadIdx.x; k < n; k += SEG_THREADS)
-                b.perm[s0 + k] = atomicAdd(&s_cell[cell[k]], 1);
+#pragma unroll
+            for (int u = 0; u < C; ++u) {
+                if (c[u] == 0xffffu) break;
+                const int rk = atomicAdd(&s_cell[c[u]], 1);
+                if (!small) b.perm[s0 + k0 + u * SEG_THREADS] = rk;
+            }
         }
         __syncthreads();
         smem_excl_scan4(s_cell, n4, ws);
@@ -339,30 +332,38 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
         if (sg == b.nseg - 1 && threadIdx.x == 0) b.cell_start[b.C] = s0 + n;
         if (small) {
             __syncthreads();  // the offsets are read before they become cursors
+            for (int k0 = threadIdx.x; k0 < n; k0 += C * SEG_THREADS) {
+                unsigned c[C];
 #pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                if (u >= mine) break;
-                const unsigned c = (cp[u / 2] >> (16 * (u & 1))) & 0xffffu;
-                s_perm[atomicAdd(&s_cell[c], 1)] = (unsigned short)(threadIdx.x + u * SEG_THREADS);
+                for (int u = 0; u < C; ++u) {
+                    const int k = k0 + u * SEG_THREADS;
+                    c[u] = k < n ? cell[k] : 0xffffu;
+                }
+#pragma unroll
+                for (int u = 0; u < C; ++u) {
+                    if (c[u] == 0xffffu) break;
+                    s_perm[atomicAdd(&s_cell[c[u]], 1)] = (unsigned short)(k0 + u * SEG_THREADS);
+                }
             }
             __syncthreads();
             const float4 *rec = b.rec + s0;
             float4 *sp = b.sp + s0;
             int32_t *sid = b.sid + s0;
             int32_t *lay = b.lay_s + s0;
-            for (int u0 = 0; u0 < mine; u0 += G) {
+            for (int q0 = threadIdx.x; q0 < n; q0 += G * SEG_THREADS) {
                 float4 v[G];
 #pragma unroll
                 for (int u = 0; u < G; ++u)
-                    if (u0 + u < mine) v[u] = rec[s_perm[threadIdx.x + (u0 + u) * SEG_THREADS]];
+                    if (q0 + u * SEG_THREADS < n) v[u] = rec[s_perm[q0 + u * SEG_THREADS]];
 #pragma unroll
-                for (int u = 0; u < G; ++u)
-                    if (u0 + u < mine) {
-                        const int q = threadIdx.x + (u0 + u) * SEG_THREADS;
+                for (int u = 0; u < G; ++u) {
+                    const int q = q0 + u * SEG_THREADS;
+                    if (q < n) {
                         sp[q] = sorted_record(v[u], fw);
                         sid[q] = __float_as_int(v[u].w);
                         lay[q] = l;
                     }
+                }
             }
         } else {
             for (int k = threadIdx.x; k < n; k += SEG_THREADS) {

@@ -52,7 +52,7 @@ cudaError_t launch_scan_segs(const Buffers &b, const LaunchCfg &c, cudaStream_t 
                                    (int32_t *)b.scan_partials, c.grid_cap, s, launches);
 }
 
-__global__ void __launch_bounds__(FILL_THREADS, 5) k_fill_place(Buffers b, Params p) {
+__global__ void __launch_bounds__(FILL_THREADS, 6) k_fill_place(Buffers b, Params p) {
     fill_place_stage(b, p);
 }
 
@@ -63,7 +63,7 @@ cudaError_t launch_fill_place(const Buffers &b, const Params &p, const LaunchCfg
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(SEG_THREADS, 2) k_fill_cells(Buffers b, Params p) {
+__global__ void __launch_bounds__(SEG_THREADS, 3) k_fill_cells(Buffers b, Params p) {
     fill_cells_stage(b, p);
 }
 
