@@ -152,10 +152,9 @@ int clue_run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t 
  * is_seed, offsets) is a HOST pointer (pinned memory is fastest).  The call
  * copies the inputs to context-owned device buffers, clusters, copies the
  * results back and returns when they are in host memory (it synchronises).
- * A batch of 8M hits or more is split at event boundaries into up to 16
- * chunks, growing by 1.25x from N/64 to N/6 and ending with a small one, and
- * pipelined over three streams: chunk c+1 is copied in and chunk c-1 copied
- * out while chunk c is clustered.
+ * A batch of 8M hits or more is split at event boundaries into chunks of
+ * about N/8 and a last one of about N/32, pipelined over three streams:
+ * chunk c+1 is copied in and chunk c-1 copied out while chunk c is clustered.
  * Errors: as clue_run_batch, including CLUE_ERR_INPUT / CLUE_ERR_TIMEOUT.
  */
 int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer,

@@ -905,19 +905,18 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
     }
     // Split the batch at event boundaries into chunks, so that the copy of
     // chunk c+1 in and the copy of chunk c-1 out overlap the clustering of
-    // chunk c.  A chunk's copy in (16 B/hit over the host link, about 13G
-    // hits/s) must end before the previous chunk's clustering (about 9G
-    // hits/s) or the device waits, so chunks grow by 1.25x from a small first
-    // one (its copy is exposed) up to N/6; the last one is again small (its
-    // copy out is exposed).  Batches below 8M hits are one chunk.
+    // chunk c.  Chunks of about N/8: a run of several million hits clusters
+    // near the full batch's rate and spreads its fixed cost (a run of 1M hits
+    // reaches only about two thirds of it), at the price of the first chunk's
+    // copy in being exposed.  The last N/32 is a chunk of its own, so little
+    // copy out is left after the clustering.  Batches below 8M hits are one
+    // chunk.
     std::vector<int32_t> cuts{0};
     if (N >= (int64_t)(8 << 20)) {
-        double want = std::max(N / 64.0, (double)(1 << 20));
-        const double cap = N / 6.0;
-        const int64_t tail = N / 32;  // hits kept for the last chunk
+        const int64_t step = N / 8, tail = N / 32;
         int64_t at = 0;
         while ((int)cuts.size() < MAX_CHUNKS - 1) {
-            const int64_t target = std::min(at + (int64_t)want, N - tail);
+            const int64_t target = std::min(at + step, N - tail);
             if (target <= at) break;
             int32_t e = cuts.back() + 1;
             while (e < n_events && offsets[e] < target) ++e;
@@ -925,7 +924,6 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
             cuts.push_back(e);
             at = offsets[e];
             if (at >= N - tail) break;
-            want = std::min(want * 1.25, cap);
         }
     }
     cuts.push_back(n_events);

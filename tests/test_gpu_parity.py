@@ -358,8 +358,8 @@ def test_host_pointer_path_pipelined_chunks(clue_mod):
 
 
 def test_host_pointer_path_tapered_chunks(clue_mod):
-    """A batch above 32M hits is cut into a small first chunk, six large ones
-    and a small last one; the results equal the device-pointer path's."""
+    """A batch above 32M hits is cut into chunks of about an eighth of it and a
+    small last one; the results equal the device-pointer path's."""
     base = [gen.make_event(n, 100, 2700 + i, "blobs")
             for i, n in enumerate([1_300_000, 700_000, 2_100_000, 40_000, 900_000])]
     evs = [base[i % len(base)] for i in range(34)]  # 34 events, about 34M hits
@@ -372,8 +372,28 @@ def test_host_pointer_path_tapered_chunks(clue_mod):
     hcid, hseed = cl.run_batch_host(x, y, l, e, offs, gen.PARAMS_BLOBS)
     assert np.array_equal(hcid, dcid) and np.array_equal(hseed, dseed)
     ref = oracle.run_event(base[3], gen.PARAMS_BLOBS, 100)
-    for i in (3, 28):  # the same small event in the second chunk and in the seventh
+    for i in (3, 28):  # the same small event in an early chunk and in a late one
         assert np.array_equal(hcid[offs[i]:offs[i + 1]], ref["cluster_id"])
+
+
+def test_host_pointer_path_error_in_a_later_chunk(clue_mod):
+    """A NaN coordinate in the second chunk of a pipelined call (the first
+    event alone fills the first chunk) is reported by the call, and the
+    context works afterwards."""
+    sizes = [1_200_000, 500_000, 2_000_000, 2_000_000, 2_000_000, 1_000_000]
+    evs = [gen.make_event(n, 100, 3700 + i, "blobs") for i, n in enumerate(sizes)]
+    x, y, l, e, offs = gen.concat(evs)
+    assert offs[-1] >= 8 << 20
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    bad = x.copy()
+    bad[offs[1] + 5] = np.nan
+    with pytest.raises(clue_mod.ClueError) as ei:
+        cl.run_batch_host(bad, y, l, e, offs, gen.PARAMS_BLOBS)
+    assert ei.value.code == clue_mod.CLUE_ERR_INPUT
+    hcid, hseed = cl.run_batch_host(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    dcid, dseed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    cl.sync()
+    assert np.array_equal(hcid, dcid.cpu().numpy()) and np.array_equal(hseed, dseed.cpu().numpy())
 
 
 def test_edge_cases(clue_mod):
