@@ -206,9 +206,11 @@ int build_plan(clue_ctx *ctx, const int64_t *offsets, int32_t E, float dc, Plan 
             ctx->msg = "grid too large: raise bin_size or shrink the extent";
             return CLUE_ERR_ARG;
         }
+        d.tile0 = (int32_t)plan.tiles.size();
         for (int64_t t = 0; t < n; t += TILE)
             plan.tiles.push_back(Tile{(int32_t)(offsets[e] + t),
                                       (int32_t)std::min<int64_t>(TILE, n - t), e, 0});
+        d.ntiles = (int32_t)plan.tiles.size() - d.tile0;
     }
     plan.N = offsets[E];
     plan.C = C;
@@ -263,13 +265,14 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t E, int64_t
     b.front_a = b.perm;  // the frontiers reuse the grid fill's scratch
     b.front_b = b.tmp;
     b.sid = b.tmp;  // the sorted ids are dead once rho has copied them
-    const int64_t parts = std::max(scan_partials_needed(N), scan_partials_needed(C)) + 1;
+    const int64_t parts =
+        std::max({scan_partials_needed(N), scan_partials_needed(C), scan_partials_needed(ntb)}) + 1;
     b.scan_partials = take((size_t)parts * 8);
     b.scan_partials_cap = parts;
     b.nseg = nseg;
-    b.seg_cnt = nseg ? (int32_t *)take((size_t)nseg * 4) : nullptr;
-    b.seg_start = nseg ? (int32_t *)take((size_t)(nseg + 1) * 4) : nullptr;
-    b.tbase = ntb ? (int32_t *)take((size_t)ntb * 4) : nullptr;
+    b.ntb = ntb;
+    b.tcount = ntb ? (int32_t *)take((size_t)ntb * 4) : nullptr;
+    b.tbase = ntb ? (int32_t *)take((size_t)(ntb + 1) * 4) : nullptr;
     b.wexp = (uint32_t *)take((size_t)E * 8);
     return off;
 }
@@ -385,10 +388,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
         return cudaEventRecordWithFlags(ctx->pev[set][ev++], s, rec_flags);
     };
     CK(cudaMemsetAsync(&b.ctrl->overflow, 0, sizeof(Ctrl) - sizeof(unsigned), s));
-    if (b.nseg)
-        CK(cudaMemsetAsync(b.seg_cnt, 0, (size_t)b.nseg * 4, s));
-    else
-        CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
+    if (!b.nseg) CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
     if (p.chase) CK(cudaMemsetAsync(b.sbits, 0, (size_t)(b.N / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(b.wexp, 0xff, (size_t)b.nevents * 8, s));
     CK(rec(nullptr));
@@ -498,7 +498,7 @@ uint64_t signature(const clue_ctx *ctx, const Plan &plan, const Buffers &b, cons
 // SCAN_SINGLE_MAX_TILES tiles).
 int pipeline_shape(const Buffers &b, const Params &p) {
     auto one = [](int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE <= SCAN_SINGLE_MAX_TILES; };
-    const int64_t first = b.nseg ? b.nseg : b.C;          // segments / cells
+    const int64_t first = b.nseg ? b.ntb : b.C;           // run table / cells
     const int64_t second = p.chase ? b.N / 32 + 1 : b.N;  // seed words / packed scan
     return (p.chase ? 1 : 0) | (one(first) ? 2 : 0) | (one(second) ? 4 : 0) | (b.nseg ? 8 : 0);
 }

@@ -34,7 +34,8 @@ struct EventDesc {
     int32_t nbx, nby;  // bins per layer along x and y
     float xmin, ymin;  // grid origin
     float inv_s;       // 1 / bin size
-    int32_t pad[2];
+    int32_t tile0;     // first tile of the event
+    int32_t ntiles;    // its tiles (0 for an empty event)
 };
 static_assert(sizeof(EventDesc) == 48, "EventDesc layout");
 
@@ -96,9 +97,13 @@ struct Buffers {
                          //     layer segments, x, y, w, id (int bits); aliases hr
     int32_t *perm;       // [N] hit ids grouped by cell, unordered within a cell
                          //     (direct sort); ranks beyond the registers (two-level)
-    int32_t *seg_cnt;    // [nseg] hits per (event, layer) segment (two-level sort)
-    int32_t *seg_start;  // [nseg + 1] segment offsets
-    int32_t *tbase;      // [ntiles * L] a tile's run in each of its layer segments
+    int32_t *tcount;     // [ntb] two-level sort: hits of each tile in each layer, by
+                         //     (event, layer, tile): event e's block starts at
+                         //     tile0 * L, layer l's column at + l * ntiles
+    int32_t *tbase;      // [ntb + 1] exclusive scan of tcount: each tile's run in
+                         //     the layered order; a segment starts at its first
+                         //     tile's entry
+    int64_t ntb;         // tiles x layers
     uint32_t *wexp;      // [2 * nevents] weight range of each event, from the fill:
                          //     min over its finite nonzero weights of max(biased
                          //     exponent, 1), and min of 255 - biased exponent
@@ -145,7 +150,7 @@ struct LaunchCfg {
 // ---- launchers (each enqueues its kernel(s) on `s`; return cudaError_t) ----
 cudaError_t launch_fill_count(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_cells(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
-// The two-level sort (b.nseg > 0): layer count, segment scan, placement, cell
+// The two-level sort (b.nseg > 0): layer count, run-table scan, placement, cell
 // sort.  fill_prepare raises the cell sort's shared-memory limit on the
 // current device; call it once per device before the first launch.
 cudaError_t fill_prepare();

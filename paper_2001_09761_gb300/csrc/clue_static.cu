@@ -173,6 +173,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     int ntiles = 0;
     for (int64_t t = 0; t < n; t += TILE)
         host.tiles[ntiles++] = Tile{(int32_t)t, (int32_t)std::min<int64_t>(TILE, n - t), 0, 0};
+    host.ev.tile0 = 0;
+    host.ev.ntiles = ntiles;
 
     b.x = x;
     b.y = y;

@@ -8,13 +8,13 @@
 // contiguous memory.  Two forms give the same layout:
 //
 //  * the two-level sort (every layer of the batch with at most SEG_MAX_CELLS
-//    cells, at most SEG_MAX_LAYERS layers): hits are first counted per
-//    (event, layer) segment with a per-tile histogram in shared memory (one
-//    global atomic per tile and layer, not one per hit), a prefix sum over the
-//    segments places them, and the records are moved into their segment; then
-//    one CTA per segment counts its hits per cell in shared memory, scans the
-//    counts and writes the cell offsets and the sorted records.  The atomics
-//    that rank hits inside a cell are shared-memory ones;
+//    cells, at most SEG_MAX_LAYERS layers): every tile counts its hits per
+//    layer in shared memory and writes the counts to a table ordered by
+//    (event, layer, tile), whose exclusive prefix sum is each tile's run in
+//    the layered order (no global atomic); the records are moved into their
+//    runs; then one CTA per (event, layer) segment counts its hits per cell in
+//    shared memory, scans the counts and writes the cell offsets and the
+//    sorted records.  The atomics that rank hits are shared-memory ones;
 //  * the direct sort (any grid): hits are counted per cell with global
 //    atomics (each returning the hit's arrival rank), a prefix sum over all
 //    cells gives the offsets, hit ids are scattered into their cell's segment
@@ -106,13 +106,19 @@ constexpr int SEG_SMEM_HITS = 16384;   // segments up to this size are permuted 
 static_assert(TILE % FILL_THREADS == 0, "tile / block");
 static_assert(SEG_SMEM_HITS <= 65536, "16-bit indices");
 
-// Layer count: the tile's hits per layer in a shared histogram, then one
-// global atomic per tile and layer reserves the tile's run in its (event,
-// layer) segment: tbase[tile * L + layer] (written for the tile's layers
-// only).  Layers outside [0, L) flag the input error and are clamped, as in
-// the direct sort.  All of a thread's loads are issued before its atomics, so
-// their latencies overlap.  Needs FILL_THREADS threads and L ints of dynamic
-// shared memory.
+// Where the run table holds (event e, layer l, tile t of e).
+// Layer l == L addresses the next event's block (the table's end for the
+// last event), so that entry l + 1 ends segment l.
+__device__ __forceinline__ int64_t run_index(const EventDesc &ev, int L, int l, int t) {
+    return (int64_t)ev.tile0 * L + (int64_t)l * ev.ntiles + (t - ev.tile0);
+}
+
+// Layer count: the tile's hits per layer in a shared histogram, written to
+// the run table (every layer, zeros included), whose exclusive prefix sum is
+// the tile's run in each of its (event, layer) segments.  Layers outside
+// [0, L) flag the input error and are clamped, as in the direct sort.  All of
+// a thread's loads are issued before its atomics, so their latencies overlap.
+// Needs FILL_THREADS threads and L ints of dynamic shared memory.
 __device__ __forceinline__ void fill_layers_stage(const Buffers &b, const Params &p) {
     extern __shared__ int s_hist[];
     constexpr int PER = TILE / FILL_THREADS;
@@ -140,11 +146,9 @@ __device__ __forceinline__ void fill_layers_stage(const Buffers &b, const Params
             }
         }
         __syncthreads();
-        const int64_t sbase = (int64_t)tl.event * p.L, tb = (int64_t)t * p.L;
-        for (int l = threadIdx.x; l < p.L; l += FILL_THREADS) {
-            const int h = s_hist[l];
-            if (h) b.tbase[tb + l] = atomicAdd(&b.seg_cnt[sbase + l], h);
-        }
+        const EventDesc ev = b.events[tl.event];
+        for (int l = threadIdx.x; l < p.L; l += FILL_THREADS)
+            b.tcount[run_index(ev, p.L, l, t)] = s_hist[l];
         __syncthreads();  // s_hist is reset for the next tile
     }
 }
@@ -254,14 +258,13 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
         }
         __syncthreads();
         // slot i of layer l goes to dst[l] + i (only the tile's layers are read)
-        const int64_t sbase = (int64_t)tl.event * p.L, tb = (int64_t)t * p.L;
+        const EventDesc ev = b.events[tl.event];
         for (int i = threadIdx.x; i < tl.len; i += FILL_THREADS) {
             const int l = s_lay[i];
             if (i == 0 || s_lay[i - 1] != l)  // first slot of the layer's run
-                s_off[l] = b.seg_start[sbase + l] + b.tbase[tb + l] - s_off[l];
+                s_off[l] = b.tbase[run_index(ev, p.L, l, t)] - s_off[l];
         }
         __syncthreads();
-        const EventDesc ev = b.events[tl.event];
         for (int i = threadIdx.x; i < tl.len; i += FILL_THREADS) {
             const float4 r = s_rec[i];
             const int dst = s_off[s_lay[i]] + i;
@@ -303,9 +306,12 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
     for (int64_t sg = blockIdx.x; sg < b.nseg; sg += gridDim.x) {
         const int e = (int)(sg / p.L);
         const int l = (int)(sg - (int64_t)e * p.L);
-        const int nbxy = b.events[e].nbx * b.events[e].nby, n4 = (nbxy + 3) / 4;
-        const int64_t cbase = b.events[e].cell_off + (int64_t)l * nbxy;
-        const int s0 = b.seg_start[sg], n = b.seg_start[sg + 1] - s0;
+        const EventDesc ev = b.events[e];
+        const int nbxy = ev.nbx * ev.nby, n4 = (nbxy + 3) / 4;
+        const int64_t cbase = ev.cell_off + (int64_t)l * nbxy;
+        // the segment runs from its first tile's run to the next segment's
+        const int s0 = b.tbase[run_index(ev, p.L, l, ev.tile0)];
+        const int n = b.tbase[run_index(ev, p.L, l + 1, ev.tile0)] - s0;
         const bool small = n <= SEG_SMEM_HITS;  // uniform over the CTA
         const FixedW fw = fixed_weights(b.wexp + 2 * e, p.chi);
         if (small && n > 0 && threadIdx.x == 0) prefetch_l2_bulk(b.rec + s0, (unsigned)n * 16u);

@@ -48,7 +48,7 @@ cudaError_t launch_fill_layers(const Buffers &b, const Params &p, const LaunchCf
 }
 
 cudaError_t launch_scan_segs(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches) {
-    return exclusive_scan<int32_t>(LoadI32{b.seg_cnt}, b.nseg, b.seg_start,
+    return exclusive_scan<int32_t>(LoadI32{b.tcount}, b.ntb, b.tbase,
                                    (int32_t *)b.scan_partials, c.grid_cap, s, launches);
 }
 

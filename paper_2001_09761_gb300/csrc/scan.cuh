@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(Load ld, int64_t n
     if (threadIdx.x == 0) out[n] = carry;
 }
 
-constexpr int64_t SCAN_SINGLE_MAX_TILES = 2;
+constexpr int64_t SCAN_SINGLE_MAX_TILES = 4;
 
 // Exclusive scan of ld(0..n-1) into out[0..n-1], out[n] = total.
 // `partials` must hold scan_partials_needed(n) elements of T.
