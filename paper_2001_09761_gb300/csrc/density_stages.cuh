@@ -178,10 +178,23 @@ __device__ __forceinline__ void rho_stage(const Buffers &b, const Params &p) {
         // the fill stored this event's records in fixed point or not (uniform)
         const FixedW fw = fixed_weights(b.wexp + 2 * tl.event, CHI);
         if (CHI == 0 && fw.on) {
+            // the next hit's record and layer are loaded while this one's
+            // window is scanned
+            float4 me_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            int lay_next = 0;
+            if ((int)threadIdx.x < tl.len) {
+                me_next = sp[tl.start + threadIdx.x];
+                lay_next = b.lay_s[tl.start + threadIdx.x];
+            }
             for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
                 const int q = tl.start + k;
-                const float4 me = sp[q];
-                const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
+                const float4 me = me_next;
+                const int lay = lay_next;
+                if (k + (int)blockDim.x < tl.len) {
+                    me_next = sp[q + blockDim.x];
+                    lay_next = b.lay_s[q + blockDim.x];
+                }
+                const int64_t plane = ev.cell_off + (int64_t)lay * nbxy;
                 const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
                 long long acc = 0;
                 unsigned T = 0;
@@ -256,11 +269,24 @@ __device__ __forceinline__ void nh_stage(const Buffers &b, const Params &p) {
         const Tile tl = b.tiles[t];
         const EventDesc ev = b.events[tl.event];
         const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
+        // the next hit's record and layer are loaded while this one's window
+        // is scanned
+        float4 me_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        int lay_next = 0;
+        if ((int)threadIdx.x < tl.len) {
+            me_next = sp[tl.start + threadIdx.x];
+            lay_next = b.lay_s[tl.start + threadIdx.x];
+        }
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
-            const float4 me = sp[q];
+            const float4 me = me_next;
+            const int lay = lay_next;
+            if (k + (int)blockDim.x < tl.len) {
+                me_next = sp[q + blockDim.x];
+                lay_next = b.lay_s[q + blockDim.x];
+            }
             const float ri = me.z;
-            const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
+            const int64_t plane = ev.cell_off + (int64_t)lay * nbxy;
             const Window w = window_of(me.x, me.y, p.rwin_nh, ev);
             // (d2, j) packed as one unsigned key: d2 >= 0, so its float bits
             // order like its value; starting at (bits(d_m^2), 0) also folds in
