@@ -101,6 +101,13 @@ __device__ __forceinline__ void assign_stage(const Buffers &b) {
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int ebase = seed_rank(b, b.events[tl.event].hit_off);
+        // the next group's codes are loaded while this group's chains are walked
+        int cn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = (int)threadIdx.x + u * (int)blockDim.x;
+            cn[u] = k < tl.len ? b.code[tl.start + k] : CODE_NOISE;
+        }
         for (int k0 = threadIdx.x; k0 < tl.len; k0 += U * blockDim.x) {
             int v[U], c[U];
             bool act[U];
@@ -109,7 +116,9 @@ __device__ __forceinline__ void assign_stage(const Buffers &b) {
                 const int k = k0 + u * (int)blockDim.x;
                 act[u] = k < tl.len;
                 v[u] = tl.start + (act[u] ? k : 0);
-                c[u] = act[u] ? b.code[v[u]] : CODE_NOISE;
+                c[u] = cn[u];
+                const int kn = k + U * (int)blockDim.x;
+                cn[u] = kn < tl.len ? b.code[tl.start + kn] : CODE_NOISE;
                 if (act[u]) b.is_seed[v[u]] = c[u] == CODE_SEED;
             }
             int64_t steps = 0;
