@@ -158,8 +158,11 @@ def test_bin_size_and_block_do_not_change_results(clue_mod, bin_size, block):
     assert_parity(_gpu_all(cl, ev, gen.PARAMS_IRREGULAR), ref)
 
 
-def test_batch_equals_events_alone(clue_mod):
-    sizes = [0, 1, 5000, 20000, 0, 1234, 40000, 7]
+@pytest.mark.parametrize("sizes", [[0, 1, 5000, 20000, 0, 1234, 40000, 7], [3000, 0, 0, 12000, 0]],
+                         ids=["mixed", "empty_last"])
+def test_batch_equals_events_alone(clue_mod, sizes):
+    """Every event of a batch (empty ones included, also as the last event,
+    where the grid fill's run table ends) clusters as it does alone."""
     evs = [gen.make_event(n, 100, 500 + i, "blobs") for i, n in enumerate(sizes)]
     x, y, l, e, offs = gen.concat(evs)
     cl = _cl(clue_mod, gen.EXTENT, 100)
@@ -255,6 +258,33 @@ def test_fixed_point_rho_at_its_bounds(clue_mod, span):
     ev2 = gen.Event(ev.x, ev.y, ev.layer, w)
     assert_parity(_gpu_all(cl, ev2, gen.PARAMS_BLOBS),
                   oracle.run(ev.x, ev.y, ev.layer, w, gen.PARAMS_BLOBS, 4))
+
+
+def test_weight_ranges_per_event_in_one_batch(clue_mod):
+    """The rho arithmetic is chosen per event from its weights: a normal
+    event (fixed point), one whose weights are all zero (no range: TwoSum),
+    one with a single nonzero weight, and one spanning 60 binary orders
+    (TwoSum), in one batch; every event matches the oracle bit for bit."""
+    evs = [gen.make_event(n, 10, 880 + i, "blobs") for i, n in enumerate([6000, 5000, 4000, 7000])]
+    rng = np.random.default_rng(88)
+    ws = [evs[0].energy,
+          np.zeros(evs[1].n, np.float32),
+          np.where(np.arange(evs[2].n) == 17, 3.5, 0.0).astype(np.float32),
+          np.ldexp(1.0, rng.integers(-30, 31, evs[3].n)).astype(np.float32)]
+    evs = [gen.Event(ev.x, ev.y, ev.layer, w) for ev, w in zip(evs, ws)]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = _cl(clue_mod, gen.EXTENT, 10)
+    cid, seed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    rho, delta, nh = cl.intermediates()
+    cl.sync()
+    cid, seed, rho, nh = (t.cpu().numpy() for t in (cid, seed, rho, nh))
+    for i, ev in enumerate(evs):
+        a, b = offs[i], offs[i + 1]
+        ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 10)
+        assert np.array_equal(_bits(rho[a:b]), _bits(ref["rho"])), i
+        assert np.array_equal(cid[a:b], ref["cluster_id"]), i
+        assert np.array_equal(seed[a:b], ref["is_seed"]), i
+        assert np.array_equal(nh[a:b], ref["nh"]), i
 
 
 def test_exact_rho_of_coincident_sets(clue_mod):
