@@ -88,15 +88,16 @@ struct Buffers {
     int64_t N;      // total hits
     int64_t C;      // total cells
     // grid
-    int32_t *key;        // [N] local cell of hit
-    int32_t *rank;       // [N] arrival rank of the hit in its cell (from the count)
-    int32_t *count;      // [C] hits per cell (zeroed per run)
+    int32_t *key;        // [N] direct sort: local cell of hit
+    int32_t *rank;       // [N] direct sort: arrival rank of the hit in its cell
+    int32_t *count;      // [C] direct sort: hits per cell (zeroed per run)
     int32_t *cell_start; // [C + 1]
     float4 *rec;         // [N] direct sort: by hit, x, y, w, local cell (int bits),
                          //     for the gather; two-level sort: by position in the
                          //     layer segments, x, y, w, id (int bits); aliases hr
-    int32_t *perm;       // [N] hit ids grouped by cell, unordered within a cell
-                         //     (direct sort); ranks beyond the registers (two-level)
+    int32_t *perm;       // [N] direct sort: hit ids grouped by cell, unordered within
+                         //     a cell; two-level sort: ranks in a segment too long to
+                         //     be permuted in shared memory
     int32_t *tcount;     // [ntb] two-level sort: hits of each tile in each layer, by
                          //     (event, layer, tile): event e's block starts at
                          //     tile0 * L, layer l's column at + l * ntiles
@@ -112,10 +113,10 @@ struct Buffers {
                              //     sort; aliases key)
     int64_t nseg;        // events x layers, or 0: the direct sort
     int32_t max_cells;   // most cells in one layer (the cell sort's shared memory)
-    int32_t *tmp;        // [N] the second expansion frontier
-    float4 *sp;          // [N] hits sorted by cell: x, y, w, id (int bits), or for an
-                         //     event on the flat kernel's fixed point x, y and the
-                         //     64-bit integer weight (two words)
+    int32_t *tmp;        // [N] the sorted ids (sid), then the second expansion frontier
+    float4 *sp;          // [N] hits sorted by (event, layer, cell): x, y, w, id (int
+                         //     bits), or for an event on the flat kernel's fixed point
+                         //     x, y and the 64-bit integer weight (two words)
     int32_t *sid;        // [N] hit id by sorted position (aliases tmp)
     int32_t *lay_s;      // [N] layer in sorted order
     // density
@@ -124,6 +125,7 @@ struct Buffers {
                          //     or -1), read only by the intermediates export
     // decision / expansion
     int32_t *code;       // [N] by hit: nh for a follower, else CODE_*; aliases key
+                         //     (and cell16: dead once the cells are sorted)
     int32_t *fcount;     // [N] followers per hit (zeroed in the fill step)
     int32_t *frank;      // [N] arrival rank of a follower in its nh's list (aliases rank)
     unsigned long long *hs;  // [N + 1] exclusive scan of (seed << 32 | followers)
