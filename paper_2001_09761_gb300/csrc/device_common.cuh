@@ -30,6 +30,17 @@ __device__ __forceinline__ void weight_range_add(unsigned *s_w, float w, bool ac
     }
 }
 
+// The same for a (lo, hi) pair a thread has already reduced over its own
+// weights (all ones: none).
+__device__ __forceinline__ void weight_range_add_bounds(unsigned *s_w, unsigned lo, unsigned hi) {
+    lo = __reduce_min_sync(FULL_MASK, lo);
+    hi = __reduce_min_sync(FULL_MASK, hi);
+    if ((threadIdx.x & 31) == 0 && lo != 0xffffffffu) {
+        atomicMin(&s_w[0], lo);
+        atomicMin(&s_w[1], hi);
+    }
+}
+
 // ... and one thread folds it into the event's after a barrier, with an atomic
 // only where it lowers the value held (which only falls, so a stale read
 // costs at most a redundant atomic).

@@ -206,13 +206,14 @@ __device__ __forceinline__ int cell_in_layer(float x, float y, const EventDesc &
 // consecutive threads write consecutive slots of a layer's run, at the run
 // the count reserved, each with its cell in the layer (16 bits, in `cell16`).
 // The layer is clamped exactly as the count clamped it.  Needs FILL_THREADS
-// threads and L ints (rounded up to a multiple of 4) of dynamic shared memory.
+// threads and 2 L ints (L rounded up to a multiple of 4) of dynamic shared
+// memory.
 __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params &p) {
     __shared__ float4 s_rec[TILE];
     __shared__ int s_lay[TILE];
     __shared__ int ws[32];
     __shared__ unsigned s_w[2];  // the tile's weight range
-    extern __shared__ int4 s_off4[];  // tile offsets by layer, then destinations
+    extern __shared__ int4 s_off4[];  // tile offsets by layer; destinations by layer
     int *s_off = reinterpret_cast<int *>(s_off4);
     constexpr int PER = TILE / FILL_THREADS;
     const int L4 = (p.L + 3) / 4;
@@ -230,9 +231,21 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
             lay[u] = b.layer[g];
         }
         __syncthreads();
+        // the weight range of this thread's hits, then of the warp (one shared
+        // atomic per warp)
+        {
+            unsigned lo = 0xffffffffu, hi = 0xffffffffu;
 #pragma unroll
-        for (int u = 0; u < PER; ++u)
-            weight_range_add(s_w, r[u].z, (int)threadIdx.x + u * FILL_THREADS < tl.len);
+            for (int u = 0; u < PER; ++u) {
+                const unsigned bits = __float_as_uint(r[u].z) & 0x7fffffffu;
+                const unsigned eb = bits >> 23;
+                if ((int)threadIdx.x + u * FILL_THREADS < tl.len && bits != 0u && eb < 255u) {
+                    lo = min(lo, max(eb, 1u));
+                    hi = min(hi, 255u - eb);
+                }
+            }
+            weight_range_add_bounds(s_w, lo, hi);
+        }
         int rk[PER];
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
@@ -259,15 +272,15 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
         __syncthreads();
         // slot i of layer l goes to dst[l] + i (only the tile's layers are read)
         const EventDesc ev = b.events[tl.event];
-        for (int i = threadIdx.x; i < tl.len; i += FILL_THREADS) {
-            const int l = s_lay[i];
-            if (i == 0 || s_lay[i - 1] != l)  // first slot of the layer's run
-                s_off[l] = b.tbase[run_index(ev, p.L, l, t)] - s_off[l];
+        int *s_dst = s_off + 4 * L4;
+        for (int l = threadIdx.x; l < p.L; l += FILL_THREADS) {
+            const int end = l + 1 < p.L ? s_off[l + 1] : tl.len;
+            if (end > s_off[l]) s_dst[l] = b.tbase[run_index(ev, p.L, l, t)] - s_off[l];
         }
         __syncthreads();
         for (int i = threadIdx.x; i < tl.len; i += FILL_THREADS) {
             const float4 r = s_rec[i];
-            const int dst = s_off[s_lay[i]] + i;
+            const int dst = s_dst[s_lay[i]] + i;
             b.rec[dst] = r;
             b.cell16[dst] = (unsigned short)cell_in_layer(r.x, r.y, ev);
         }

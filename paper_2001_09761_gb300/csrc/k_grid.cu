@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(FILL_THREADS, 6) k_fill_place(Buffers b, Param
 cudaError_t launch_fill_place(const Buffers &b, const Params &p, const LaunchCfg &, cudaStream_t s) {
     if (p.L < 1 || p.L > SEG_MAX_LAYERS) return cudaErrorInvalidValue;
     const int grid = b.ntiles;
-    k_fill_place<<<grid > 0 ? grid : 1, FILL_THREADS, (size_t)(p.L + 3) / 4 * 16, s>>>(b, p);
+    k_fill_place<<<grid > 0 ? grid : 1, FILL_THREADS, (size_t)(p.L + 3) / 4 * 32, s>>>(b, p);
     return cudaGetLastError();
 }
 
