@@ -25,8 +25,9 @@ cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, c
 
 __global__ void __launch_bounds__(256, 2) k_assign(Buffers b) { assign_stage(b); }
 
-cudaError_t launch_assign(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
-    const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
+// One CTA per tile (chain lengths vary; see launch_rho).
+cudaError_t launch_assign(const Buffers &b, const LaunchCfg &, cudaStream_t s) {
+    const int grid = b.ntiles;
     k_assign<<<grid > 0 ? grid : 1, 256, 0, s>>>(b);
     return cudaGetLastError();
 }

@@ -7,8 +7,10 @@ namespace clue {
 template <int CHI>
 __global__ void __launch_bounds__(256) k_rho(Buffers b, Params p) { rho_stage<CHI>(b, p); }
 
+// One CTA per tile: hits differ widely in window population, and the
+// hardware's CTA scheduling balances that better than a persistent grid.
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
-    const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
+    const int grid = b.ntiles;
     const int g = grid > 0 ? grid : 1;
     if (p.chi == 1)
         k_rho<1><<<g, c.block_density, 0, s>>>(b, p);
@@ -22,7 +24,7 @@ cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cu
 __global__ void __launch_bounds__(256) k_nh(Buffers b, Params p) { nh_stage(b, p); }
 
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
-    const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
+    const int grid = b.ntiles;
     k_nh<<<grid > 0 ? grid : 1, c.block_density, 0, s>>>(b, p);
     return cudaGetLastError();
 }
