@@ -99,7 +99,7 @@ struct clue_ctx {
     Ctrl *d_ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;
     float bin_scale[NCLASS];
-    int block_density = 256;
+    int block_density = 128;  // threads per CTA of rho / nh (one CTA per tile)
     bool profiling = false;
     // ring of event sets: profiled run r stamps set r % NPSETS
     cudaEvent_t pev[NPSETS][NPROF] = {};

@@ -205,7 +205,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     prm.chi_inv = 1.0f;
     LaunchCfg cfg;
     cfg.block_fill = 256;
-    cfg.block_density = 256;
+    cfg.block_density = 128;
     cfg.grid_cap = sms * 8;
 
 #define SCK(call)                                            \
