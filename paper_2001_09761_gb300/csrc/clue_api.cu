@@ -99,7 +99,7 @@ struct clue_ctx {
     Ctrl *d_ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;
     float bin_scale[NCLASS];
-    int block_density = 128;  // threads per CTA of rho / nh (one CTA per tile)
+    int block_density = 0;  // threads per CTA of rho / nh (one CTA per tile); 0: by run size
     bool profiling = false;
     // ring of event sets: profiled run r stamps set r % NPSETS
     cudaEvent_t pev[NPSETS][NPROF] = {};
@@ -357,10 +357,17 @@ int upload_tables_async(clue_ctx *ctx, const Plan &plan) {
     return CLUE_OK;
 }
 
-LaunchCfg make_cfg(const clue_ctx *ctx) {
+// The density kernels run one CTA per tile.  Unless the options or the
+// tuning table fix their block size, a run with enough tiles to give every SM
+// eight CTAs uses 128 threads (eight hits per thread; finer CTAs balance the
+// uneven windows better), a smaller one 256 (more threads on the few tiles).
+LaunchCfg make_cfg(const clue_ctx *ctx, int64_t ntiles) {
     LaunchCfg c;
     c.block_fill = 256;
-    c.block_density = ctx->opts.block_size > 0 ? ctx->opts.block_size : ctx->block_density;
+    const int automatic = ntiles >= 8LL * ctx->num_sms ? 128 : 256;
+    c.block_density = ctx->opts.block_size > 0 ? ctx->opts.block_size
+                    : ctx->block_density > 0   ? ctx->block_density
+                                               : automatic;
     c.grid_cap = ctx->num_sms * 8;
     return c;
 }
@@ -585,7 +592,7 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     b.is_seed = is_seed;
     b.ctrl = ctx->d_ctrl;
     const Params p = make_params(ctx, dc, rhoc, delta_c, delta_o);
-    const LaunchCfg cfg = make_cfg(ctx);
+    const LaunchCfg cfg = make_cfg(ctx, (int64_t)plan.tiles.size());
 
     const bool graphs = allow_graph && ctx->opts.use_graphs && ctx->stream != nullptr;
     if (graphs) {
@@ -1165,7 +1172,7 @@ int clue_set_tuning(clue_ctx *ctx, const char *text) {
             if (k < 0 || !(sc >= 0.25f && sc <= 64.0f)) return CLUE_ERR_ARG;
             scale[k] = sc;
         } else if (std::sscanf(line.c_str(), "block %d %c", &bl, &tail) == 1) {
-            if (bl < 32 || bl > 256 || bl % 32) return CLUE_ERR_ARG;
+            if (bl != 0 && (bl < 32 || bl > 256 || bl % 32)) return CLUE_ERR_ARG;  // 0: by run size
             block = bl;
         } else {
             return CLUE_ERR_ARG;
