@@ -394,10 +394,16 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
         if (name) ctx->prof_names[set].push_back(name);
         return cudaEventRecordWithFlags(ctx->pev[set][ev++], s, rec_flags);
     };
-    CK(cudaMemsetAsync(&b.ctrl->overflow, 0, sizeof(Ctrl) - sizeof(unsigned), s));
-    if (!b.nseg) CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
-    if (p.chase) CK(cudaMemsetAsync(b.sbits, 0, (size_t)(b.N / 32 + 1) * 4, s));
-    CK(cudaMemsetAsync(b.wexp, 0xff, (size_t)b.nevents * 8, s));
+    // The two-level sort's first kernel resets the run's control words, weight
+    // ranges and seed bits itself (memset nodes cost a run of a small event
+    // several microseconds); the direct sort needs them, and its cell
+    // counters, set beforehand.
+    if (!b.nseg) {
+        CK(cudaMemsetAsync(&b.ctrl->overflow, 0, sizeof(Ctrl) - sizeof(unsigned), s));
+        CK(cudaMemsetAsync(b.count, 0, (size_t)b.C * 4, s));
+        if (p.chase) CK(cudaMemsetAsync(b.sbits, 0, (size_t)(b.N / 32 + 1) * 4, s));
+        CK(cudaMemsetAsync(b.wexp, 0xff, (size_t)b.nevents * 8, s));
+    }
     CK(rec(nullptr));
     if (b.nseg) {  // two-level sort: layer segments, then cells
         CK(launch_fill_layers(b, p, cfg, s));

@@ -118,13 +118,28 @@ __device__ __forceinline__ int64_t run_index(const EventDesc &ev, int L, int l, 
 // the tile's run in each of its (event, layer) segments.  Layers outside
 // [0, L) flag the input error and are clamped, as in the direct sort.  All of
 // a thread's loads are issued before its atomics, so their latencies overlap.
-// Needs FILL_THREADS threads and L ints of dynamic shared memory.
+// As the run's first kernel it also resets what later kernels accumulate
+// into: the control words (CTA 0), the event's weight range (its first tile)
+// and, in chase mode, the seed-bit words of the tile's hits (and the word
+// after them, so that the word past the last hit is clear too).  Needs
+// FILL_THREADS threads and L ints of dynamic shared memory.
 __device__ __forceinline__ void fill_layers_stage(const Buffers &b, const Params &p) {
     extern __shared__ int s_hist[];
     constexpr int PER = TILE / FILL_THREADS;
+    static_assert(FILL_THREADS >= TILE / 32 + 2, "one thread per seed-bit word");
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        b.ctrl->overflow = 0u;
+        b.ctrl->fsize[0] = b.ctrl->fsize[1] = b.ctrl->fsize[2] = 0;
+    }
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         for (int l = threadIdx.x; l < p.L; l += FILL_THREADS) s_hist[l] = 0;
+        if (t == b.events[tl.event].tile0 && threadIdx.x < 2)
+            b.wexp[2 * tl.event + threadIdx.x] = 0xffffffffu;
+        if (p.chase) {
+            const int w0 = tl.start >> 5, w1 = (tl.start + tl.len) >> 5;
+            if ((int)threadIdx.x <= w1 - w0) b.sbits[w0 + threadIdx.x] = 0u;
+        }
         int lay[PER];
 #pragma unroll
         for (int u = 0; u < PER; ++u) {

@@ -120,16 +120,22 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(Load ld, int64_t n, 
     scan_down_stage<T, Load>(ld, n, partials, out, ntiles);
 }
 
-// The whole scan in one CTA, tile after tile with a running carry: for inputs
-// of a few tiles, where three launches cost more than the work.
+// The whole scan in one CTA of SCAN_SINGLE_THREADS, tile after tile of
+// SCAN_SINGLE_TILE with a running carry: for small inputs, where three
+// launches cost more than the work (one pass up to SCAN_SINGLE_TILE entries).
+constexpr int SCAN_SINGLE_THREADS = 1024;
+constexpr int64_t SCAN_SINGLE_TILE = (int64_t)SCAN_SINGLE_THREADS * SCAN_ITEMS;
+
 template <typename T, typename Load>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(Load ld, int64_t n, T *out,
-                                                              int64_t ntiles) {
-    __shared__ T wsum[SCAN_THREADS / 32];
+__global__ void __launch_bounds__(SCAN_SINGLE_THREADS) k_scan_single(Load ld, int64_t n, T *out) {
+    static_assert(SCAN_SINGLE_THREADS == 32 * 32, "one warp scans the warps' totals");
+    __shared__ T wsum[32];
+    __shared__ T wtotal;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T carry = 0;  // the same in every thread
+    const int64_t ntiles = (n + SCAN_SINGLE_TILE - 1) / SCAN_SINGLE_TILE;
     for (int64_t t = 0; t < ntiles; ++t) {
-        const int64_t base = t * SCAN_TILE + (int64_t)warp * 32 * SCAN_ITEMS;
+        const int64_t base = t * SCAN_SINGLE_TILE + (int64_t)warp * 32 * SCAN_ITEMS;
         T ex[SCAN_ITEMS];
         T run = 0;
 #pragma unroll
@@ -142,11 +148,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(Load ld, int64_t n
         }
         if (lane == 0) wsum[warp] = run;
         __syncthreads();
-        T off = carry, total = 0;
-        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
-            off += w < warp ? wsum[w] : T(0);
-            total += wsum[w];
+        if (warp == 0) {  // the warps' totals, scanned by one warp
+            const T v = wsum[lane];
+            const T incl = warp_incl_scan(v);
+            wsum[lane] = incl - v;
+            if (lane == 31) wtotal = incl;
         }
+        __syncthreads();
+        const T off = carry + wsum[warp], total = wtotal;
 #pragma unroll
         for (int i = 0; i < SCAN_ITEMS; ++i) {
             const int64_t idx = base + (int64_t)i * 32 + lane;
@@ -167,7 +176,7 @@ cudaError_t exclusive_scan(Load ld, int64_t n, T *out, T *partials, int grid_cap
                            int *launches) {
     const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntiles <= SCAN_SINGLE_MAX_TILES) {
-        k_scan_single<T, Load><<<1, SCAN_THREADS, 0, s>>>(ld, n, out, ntiles);
+        k_scan_single<T, Load><<<1, SCAN_SINGLE_THREADS, 0, s>>>(ld, n, out);
         if (launches) *launches += 1;
         return cudaGetLastError();
     }
