@@ -72,7 +72,8 @@ typedef struct clue_opts {
     int32_t block_size;  /* threads per block of the density kernels (32..256, a
                             multiple of 32); 0 = from the tuning table, whose
                             default (block 0) picks 128 for runs of at least
-                            8 tiles of 1024 hits per SM and 256 below */
+                            8 tiles of 1024 hits per SM, 256 for at least one
+                            tile per SM and 1024 below */
     int32_t use_graphs;  /* 1 = capture a repeated call into a CUDA graph and replay it */
     void *stream;        /* cudaStream_t to queue work on; NULL = context-owned stream */
     int32_t expand;      /* how ids reach the followers (identical results):

@@ -360,11 +360,12 @@ int upload_tables_async(clue_ctx *ctx, const Plan &plan) {
 // The density kernels run one CTA per tile.  Unless the options or the
 // tuning table fix their block size, a run with enough tiles to give every SM
 // eight CTAs uses 128 threads (eight hits per thread; finer CTAs balance the
-// uneven windows better), a smaller one 256 (more threads on the few tiles).
+// uneven windows better), one with at least a tile per SM 256, and a smaller
+// one 1024 (one hit per thread: its few tiles' hits all in flight at once).
 LaunchCfg make_cfg(const clue_ctx *ctx, int64_t ntiles) {
     LaunchCfg c;
     c.block_fill = 256;
-    const int automatic = ntiles >= 8LL * ctx->num_sms ? 128 : 256;
+    const int automatic = ntiles >= 8LL * ctx->num_sms ? 128 : ntiles >= ctx->num_sms ? 256 : 1024;
     c.block_density = ctx->opts.block_size > 0 ? ctx->opts.block_size
                     : ctx->block_density > 0   ? ctx->block_density
                                                : automatic;
@@ -507,13 +508,16 @@ uint64_t signature(const clue_ctx *ctx, const Plan &plan, const Buffers &b, cons
 }
 
 // The shape of a run's launch sequence: expansion mode, form of the grid
-// fill and, for each prefix sum, whether it runs in one CTA (at most
-// SCAN_SINGLE_MAX_TILES tiles).
-int pipeline_shape(const Buffers &b, const Params &p) {
+// fill, the density kernels' build (CTAs above 256 threads use another
+// kernel, which an executable graph's update cannot swap in) and, for each
+// prefix sum, whether it runs in one CTA (at most SCAN_SINGLE_MAX_TILES
+// tiles).
+int pipeline_shape(const Buffers &b, const Params &p, const LaunchCfg &cfg) {
     auto one = [](int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE <= SCAN_SINGLE_MAX_TILES; };
     const int64_t first = b.nseg ? b.ntb : b.C;           // run table / cells
     const int64_t second = p.chase ? b.N / 32 + 1 : b.N;  // seed words / packed scan
-    return (p.chase ? 1 : 0) | (one(first) ? 2 : 0) | (one(second) ? 4 : 0) | (b.nseg ? 8 : 0);
+    return (p.chase ? 1 : 0) | (one(first) ? 2 : 0) | (one(second) ? 4 : 0) | (b.nseg ? 8 : 0) |
+           (cfg.block_density > 256 ? 16 : 0);
 }
 
 // Queue a run whose exact signature has no cached graph: capture it, and
@@ -534,7 +538,7 @@ int enqueue_via_template(clue_ctx *ctx, const Buffers &b, const Params &p, const
         if (graph) cudaGraphDestroy(graph);
         return cuda_fail(ctx, e, "graph capture");
     }
-    cudaGraphExec_t &ex = ctx->templates[pipeline_shape(b, p)];
+    cudaGraphExec_t &ex = ctx->templates[pipeline_shape(b, p, cfg)];
     bool updated = false;
     if (ex) {
         cudaGraphExecUpdateResultInfo info;
