@@ -661,7 +661,7 @@ def test_scratch_limit_fails_cleanly_then_recovers(clue_mod):
 
 def test_unit_weight_partition_invariant_under_permutation(clue_mod):
     """With unit weights rho is an exact integer, so relabelling the hits only
-    relabels the clusters (SURVEY T7), on the GPU path."""
+    relabels the clusters, on the GPU path."""
     ev = gen.make_event(300_000, 100, 5, "paper")
     perm = np.random.default_rng(2).permutation(ev.n)
     cl = _cl(clue_mod, gen.EXTENT, 100)
