@@ -253,16 +253,21 @@ int64_t clue_scratch_bytes(clue_ctx *ctx);
  *   n          0 <= n <= CLUE_STATIC_MAX_HITS (larger n: CLUE_ERR_ARG, nothing runs)
  *   dc, rhoc, delta_c, delta_o: as in clue_run
  *   x_min..y_max, max_layers: the grid extent and layer count (as clue_opts);
- *     max_layers * (bins per layer) must fit CLUE_STATIC_MAX_CELLS, else the
- *     bins are widened (results do not depend on the bin size)
+ *     1 <= max_layers <= CLUE_STATIC_MAX_CELLS; the bins are widened until
+ *     max_layers * (bins per layer) fits CLUE_STATIC_MAX_CELLS (results do not
+ *     depend on the bin size)
  *   stream     cudaStream_t to run on (NULL = the legacy default stream)
  *
  * The call is synchronous: it returns after the results are in cluster_id /
  * is_seed, with CLUE_OK, CLUE_ERR_ARG, CLUE_ERR_INPUT (NaN/Inf or bad layer,
- * outputs unspecified), CLUE_ERR_TIMEOUT or CLUE_ERR_CUDA.
- * The first call on each device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and keeps what the previous call
+ * outputs unspecified), CLUE_ERR_TIMEOUT, CLUE_ERR_OOM (first call on a
+ * device only, see below) or CLUE_ERR_CUDA.
+ * The first call on each device sets the call up there (once per device,
+ * with that device current): it loads the library's device code on that
+ * device, which reserves the array, and looks up the array's device address.
+ * That first call can therefore block, and it fails with CLUE_ERR_OOM when
+ * the device has no room left for the array; make it at set-up time, before
+ * any stream capture.  Later calls on that device allocate nothing.  Every call shares the one array and keeps what the previous call
  * left in it (the call clears what must start at zero): calls that overlap on
  * the GPU -- from several host threads or on several streams at once -- race
  * and give wrong results.

@@ -236,6 +236,8 @@ def clue_version() -> str:
 
 #: Largest event clue_run_static accepts (CLUE_STATIC_MAX_HITS).
 CLUE_STATIC_MAX_HITS = 65536
+#: Most grid cells (layers x bins per layer) clue_run_static's array holds.
+CLUE_STATIC_MAX_CELLS = 1048576
 
 
 def clue_run_static(x, y, layer, energy, n, dc, rhoc, delta_c, delta_o, x_min, x_max, y_min,

@@ -61,10 +61,13 @@ int scratch_address(int dev, void **out) {
     if (dev < 0 || dev >= MAX_DEVICES) return CLUE_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
+        // The first use on a device loads the library's device code there and
+        // reserves the array; without room for it that fails as an allocation.
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
             cudaGetLastError();
-            return CLUE_ERR_CUDA;
+            return e == cudaErrorMemoryAllocation ? CLUE_ERR_OOM : CLUE_ERR_CUDA;
         }
         g_scratch_ptr[dev] = p;
     }
@@ -103,18 +106,24 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
         return CLUE_ERR_CUDA;
 
     // Grid: the bin size only changes speed, never results; widen the bins
-    // until the grid fits the static cell budget.
+    // until the grid fits the static cell budget.  Every size test is done in
+    // double precision on the bin counts as reals, so no integer product or
+    // int32 store happens before the grid is known to fit.
     const double wx = (double)x_max - x_min, wy = (double)y_max - y_min;
-    double sbin = std::max((double)dc, 6.0 * dc * 1.001);
-    int64_t nbx = 1, nby = 1;
     const double cap = std::min<double>(16.0 * (double)n + 64.0 * max_layers,
                                         (double)STATIC_MAX_CELLS);
-    for (int it = 0; it < 200; ++it) {
-        nbx = std::max<int64_t>(1, (int64_t)std::ceil(wx / sbin));
-        nby = std::max<int64_t>(1, (int64_t)std::ceil(wy / sbin));
-        if ((double)nbx * nby * max_layers <= cap) break;
-        sbin *= 1.1;
+    double sbin = std::max((double)dc, 6.0 * dc * 1.001);
+    double fx = 1.0, fy = 1.0;  // bins per axis as reals
+    bool fits = false;
+    for (int it = 0; it < 64 && !fits; ++it) {
+        fx = std::max(1.0, std::ceil(wx / sbin));
+        fy = std::max(1.0, std::ceil(wy / sbin));
+        const double cells = fx * fy * (double)max_layers;
+        fits = cells <= cap && fx <= (double)(1 << 20) && fy <= (double)(1 << 20);
+        if (!fits) sbin *= std::max(1.05, std::sqrt(cells / cap));
     }
+    if (!fits) return CLUE_ERR_ARG;  // no bin size gives a grid within the budget
+    const int64_t nbx = (int64_t)fx, nby = (int64_t)fy;
     const int64_t C = (int64_t)max_layers * nbx * nby;
     if (C > STATIC_MAX_CELLS) return CLUE_ERR_ARG;
 

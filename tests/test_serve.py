@@ -1,5 +1,6 @@
 """Continuous-batching server: scheduling on CPU with a fake backend, and on
-the GPU each served result against the same event clustered alone."""
+the GPU each served result against the oracle's clustering of the event
+alone."""
 from __future__ import annotations
 
 import threading
@@ -123,10 +124,12 @@ def test_offered_load_driver_poisson():
 
 @pytest.mark.gpu
 def test_served_results_equal_events_alone():
+    """Served events (batched with others of every size) against the oracle,
+    element by element: each result is the one the event has alone."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2001_09761_gb300 import clue
+    import oracle
     from paper_2001_09761_gb300.serve import GpuBackend
     rng = np.random.default_rng(5)
     sizes = [int(v) for v in np.exp(rng.uniform(np.log(1e3), np.log(4e5), 30))] + [1, 0, 7]
@@ -138,9 +141,40 @@ def test_served_results_equal_events_alone():
     results = [f.result(timeout=120) for f in futs]
     srv.close()
     assert srv.stats()["batches"] < len(events)  # events really were batched
-    cl = clue.Clusterer(device=0, extent=gen.EXTENT, max_layers=100)
     for ev, (cid, seed) in zip(events, results):
-        a_cid, a_seed = cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_BLOBS)
-        cl.sync()
-        assert np.array_equal(cid.cpu().numpy(), a_cid.cpu().numpy())
-        assert np.array_equal(seed.cpu().numpy(), a_seed.cpu().numpy())
+        ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 100)
+        assert np.array_equal(cid.cpu().numpy(), ref["cluster_id"])
+        assert np.array_equal(seed.cpu().numpy(), ref["is_seed"])
+
+
+@pytest.mark.gpu
+def test_served_stream_up_to_2M_hit_events():
+    """The served stream's size range (log-uniform 10k-2M hits, 100 layers,
+    one event of exactly 2M) through the benchmark's server configuration
+    (16M-hit regions, three of them, results on the host), with Poisson
+    arrivals; every result against the oracle."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_2001_09761_gb300.serve import GpuBackend
+    sizes = [int(v) for v in gen.batch_sizes(11, 1e4, 2e6, seed=7)] + [2_000_000]
+    events = [gen.make_event(n, 100, 6000 + k, "blobs") for k, n in enumerate(sizes)]
+    pool = [(ev.x, ev.y, ev.layer, ev.energy) for ev in events]
+    be = GpuBackend(device=0, extent=gen.EXTENT, max_layers=100, params=gen.PARAMS_BLOBS,
+                    region_hits=16_000_000, n_regions=3, host_results=True)
+    srv = Server(be)
+    rng = np.random.default_rng(11)
+    futs = []
+    for k in rng.permutation(len(pool)).tolist() + [len(pool) - 1]:
+        futs.append((k, srv.submit(*pool[k])))
+        time.sleep(float(rng.exponential(0.002)))
+    results = [(k, f.result(timeout=300)) for k, f in futs]
+    srv.close()
+    refs = {}
+    for k, (cid, seed) in results:
+        if k not in refs:
+            refs[k] = oracle.run_event(events[k], gen.PARAMS_BLOBS, 100)
+        assert np.array_equal(np.asarray(cid), refs[k]["cluster_id"]), f"event {k}"
+        assert np.array_equal(np.asarray(seed), refs[k]["is_seed"]), f"event {k}"
+    assert max(sizes) == 2_000_000

@@ -57,6 +57,39 @@ def test_static_scratch_entry_point_matches_clue_run():
         assert (ref_cid >= 0).any() and (ref_cid < 0).any()
 
 
+def _ref(clue, ev, params, extent, layers):
+    cl = clue.Clusterer(device=0, extent=extent, max_layers=layers)
+    cid, seed = cl.run(ev.x, ev.y, ev.layer, ev.energy, params)
+    cl.sync()
+    out = cid.cpu().numpy(), seed.cpu().numpy()
+    cl.close()
+    return out
+
+
+def test_static_entry_point_at_its_limits():
+    """The largest event the array holds (CLUE_STATIC_MAX_HITS hits, 64 full
+    tiles) on a grid of 1000 layers, whose first bin size gives more cells
+    than the array holds, so the bins are widened several times; then a tiny
+    d_c, whose first grid would overflow any integer, widened to fit as well.
+    Both give clue_run's results (the bin size never changes them)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_09761_gb300 import clue
+    clue.load()
+    stream = torch.cuda.Stream()
+    n = clue.CLUE_STATIC_MAX_HITS
+    ev = gen.make_event(n, 1000, 43, "blobs")
+    assert ev.n == n and int(ev.layer.max()) == 999
+    tiny = (1e-15, 0.5, 2.0, 4.0)  # only coincident hits are within d_c
+    for params in (gen.PARAMS_BLOBS, tiny):
+        ref_cid, ref_seed = _ref(clue, ev, params, gen.EXTENT, 1000)
+        rc, cid, seed = _static(clue, torch, ev, params, gen.EXTENT, 1000, stream.cuda_stream)
+        assert rc == clue.CLUE_OK, clue.clue_strerror(rc)
+        assert np.array_equal(cid, ref_cid)
+        assert np.array_equal(seed, ref_seed)
+
+
 def test_static_entry_point_rejects_oversized_events():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -66,4 +99,17 @@ def test_static_entry_point_rejects_oversized_events():
     n = clue.CLUE_STATIC_MAX_HITS + 1
     rc = clue.clue_run_static(1, 1, 1, 1, n, 2.0, 2.0, 2.0, 4.0, -250.0, 250.0, -250.0, 250.0,
                               100, 1, 1, None)
+    assert rc == clue.CLUE_ERR_ARG
+
+
+def test_static_entry_point_rejects_too_many_layers():
+    """More layers than the array has cells: no bin size can fit, so the call
+    is refused before anything runs."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_09761_gb300 import clue
+    clue.load()
+    rc = clue.clue_run_static(1, 1, 1, 1, 100, 2.0, 2.0, 2.0, 4.0, -250.0, 250.0, -250.0, 250.0,
+                              clue.CLUE_STATIC_MAX_CELLS + 1, 1, 1, None)
     assert rc == clue.CLUE_ERR_ARG
