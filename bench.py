@@ -183,7 +183,29 @@ ALG_BYTES = {
     "assign": 4 + 4 + 4 + 1,           # code, the nh's code, seed bits in; id, seed flag out
     "expand_level": 8 + 4 + 4 + 4,     # list range, parent id, follower in; id out
     "complete": 4 + 4,                 # id in, id out
+    "jump": 0,                         # nothing unless a chain outruns the bounded walk
 }
+
+
+# The staged floor per pipeline step, in bytes per hit (each step reads what
+# it needs once and writes its result once, at minimal width): S1 grid fill
+# 12 B read + 4 B index written; S2 rho 12 B gathered + 4 B written; S3
+# nh/delta 12 B + 4 B rho read, 8 B (nh, delta^2) written; S4 decision 8 B
+# read + 5 B written + 8 B follower lists; S5 expansion 8 B.  85 B/hit in all;
+# the compulsory input and output alone are 16 + 5 = 21 B/hit.
+STAGED_BYTES = {"S1": 16, "S2": 16, "S3": 24, "S4": 21, "S5": 8}
+STEP_OF_KERNEL = {"fill_layers": "S1", "fill_place": "S1", "fill_cells": "S1",
+                  "fill_count": "S1", "fill_scatter": "S1", "fill_canon": "S1",
+                  "rho": "S2", "nh_delta": "S3", "density": "S2+S3",
+                  "scan_hits": "S4", "link": "S4", "assign": "S4+S5",
+                  "expand_level": "S5", "complete": "S5", "jump": "S5"}
+COMPULSORY_BYTES = 21
+STAGED_TOTAL = sum(STAGED_BYTES.values())
+
+
+def staged_bytes(kernel):
+    """The staged-floor bytes per hit of the step(s) a kernel carries out."""
+    return sum(STAGED_BYTES[s] for s in STEP_OF_KERNEL[kernel].split("+"))
 
 
 def parse_traffic():
@@ -264,7 +286,7 @@ def extra_configs(torch, clue, tuning, dev, args):
 
     res["single_10k"] = single(gen.single_event_10k(0), 10, PARAMS, 200, "c1")
     sweep = {}
-    for h in range(1000, 10001, 1000 if args.full else 3000):
+    for h in range(1000, 10001, 3000 if args.quick else 1000):
         vals = [single(gen.scaling_event(h, s), 100, PARAMS, 10, "c2")["mhits_per_s"]
                 for s in range(args.sweep_seeds)]
         sweep[str(100 * h)] = float(np.median(vals))
@@ -336,11 +358,12 @@ def main():
     ap.add_argument("--per-event-sample", type=int, default=64)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
-    ap.add_argument("--full", action="store_true", help="full sweep and request counts")
-    ap.add_argument("--sweep-seeds", type=int, default=2)
+    ap.add_argument("--quick", action="store_true",
+                    help="4 sweep sizes x 2 seeds, 300 requests at loads 0.1, 0.5, 0.9")
+    ap.add_argument("--sweep-seeds", type=int, default=10)
     ap.add_argument("--pool", type=int, default=32)
-    ap.add_argument("--requests", type=int, default=300)
-    ap.add_argument("--loads", type=float, nargs="*", default=[0.1, 0.5, 0.9])
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--loads", type=float, nargs="*", default=[0.1, 0.25, 0.5, 0.75, 0.9, 1.0])
     ap.add_argument("--profile-case", action="store_true",
                     help="run the ncu case only: the batch's first 40 events, twice")
     args = ap.parse_args()
@@ -348,9 +371,9 @@ def main():
         return profile_case()
     if args.warmup < 3:
         args.warmup = 3
-    if args.full:
-        args.sweep_seeds, args.requests = 10, 2000
-        args.loads = [0.1, 0.25, 0.5, 0.75, 0.9, 1.0]
+    if args.quick:
+        args.sweep_seeds, args.requests = 2, 300
+        args.loads = [0.1, 0.5, 0.9]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -507,18 +530,31 @@ def main():
     cl_h.close()
 
     # ---- roofline of the dominant kernel ------------------------------------
+    # achieved = the staged-floor bytes of the kernel's step(s) per hit x the
+    # hits of one launch / the kernel's CUDA-event time per launch
     dom = max((k for k in kern if k in ALG_BYTES), key=kern.get)
     peak, peak_kind = load_peaks()
-    achieved = ALG_BYTES[dom] * N / (kern[dom] * 1e-3) / 1e9
+    sec = kern[dom] * 1e-3
+    achieved = staged_bytes(dom) * N / sec / 1e9
     traffic, issue = None, None
     tr = parse_traffic()
     if dom in tr and tr[dom][1] == source_hash():
         traffic = tr[dom][0] * N
         issue = tr[dom][2]
+    step_s = ms_per_step * 1e-3
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
-                "alg_bytes_per_hit": ALG_BYTES[dom],
+                "bytes_model": f"staged floor of step {STEP_OF_KERNEL[dom]}: "
+                               f"{staged_bytes(dom)} B/hit",
+                "alg_bytes_per_hit": staged_bytes(dom),
+                # the same kernel against every array it really moves once
+                # (packed id and decision code included)
+                "kernel_bytes_per_hit": ALG_BYTES[dom],
+                "kernel_bytes_frac": ALG_BYTES[dom] * N / sec / 1e9 / peak,
+                # the whole step against the compulsory I/O and the staged floor
+                "step_frac_compulsory_21B": COMPULSORY_BYTES * hits_all / ws / step_s / 1e9 / peak,
+                "step_frac_staged_85B": STAGED_TOTAL * hits_all / ws / step_s / 1e9 / peak,
                 # ncu's share of cycles issuing an instruction (same capture as
                 # traffic): the density kernels are bound by issue, not bytes
                 "ncu_issue_active": issue,
@@ -534,6 +570,33 @@ def main():
         cpu = {"value": v, "unit": "Mhits/s", "cores": 1, "kind": "oracle", "sample": desc}
 
     if rank == 0:
+        per_event = {"value": per_event_value, "unit": "Mhits/s", "events": len(idx),
+                     "hits": pe_hits,
+                     "kind": "one clue_run per event, back to back, each event new to the "
+                             "context"}
+        latency = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                   "kind": "one event alone (new to the context), device-resident input, "
+                           "launch to sync"}
+        frontier = {"value": frontier_value, "unit": "Mhits/s",
+                    "kind": "same batch, CLUE_EXPAND_FRONTIER"}
+        e2e = {"value": e2e_value, "unit": "Mhits/s", "h2d_bytes_per_step": 16 * N,
+               "d2h_bytes_per_step": 5 * N, "matches_device_path": ok}
+        # the compact view of every figure, last on the line so a kept tail of
+        # the output still shows it
+        summary = {"batched_mhits_per_s": value, "e2e_mhits_per_s": e2e_value,
+                   "per_event_mhits_per_s": per_event_value,
+                   "frontier_mhits_per_s": frontier_value,
+                   "event_latency_ms_p50_p99": [latency["p50"], latency["p99"]],
+                   "dominant_kernel": dom, "dominant_frac_of_hbm": roofline["frac"],
+                   "step_frac_compulsory_21B": roofline["step_frac_compulsory_21B"]}
+        if extra:
+            summary["single_10k_mhits_per_s"] = extra["single_10k"]["mhits_per_s"]
+            summary["irregular_5M_mhits_per_s"] = extra["irregular_5M"]["mhits_per_s"]
+            summary["sweep_median_mhits_per_s"] = extra["scaling_sweep_median_mhits_per_s"]
+        if srv:
+            summary["served"] = {k: [v["mhits_per_s"], v["p50_ms"], v["p99_ms"]]
+                                 for k, v in srv["loads"].items()}
+            summary["served_fields"] = "load: [Mhits/s, p50 ms, p99 ms]"
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "Mhits/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -542,25 +605,18 @@ def main():
             "config": {"workload": WORKLOAD, "global_batch": len(events) * ws,
                        "hits_per_step": hits_all, "parallelism": f"replicas x{ws}",
                        "l2": "inputs (1 GB per rank) larger than L2, no flush"},
-            "batched_frontier_expansion": {"value": frontier_value, "unit": "Mhits/s",
-                                           "kind": "same batch, CLUE_EXPAND_FRONTIER"},
-            "per_event": {"value": per_event_value, "unit": "Mhits/s", "events": len(idx),
-                          "hits": pe_hits,
-                          "kind": "one clue_run per event, back to back, each event new to "
-                                  "the context"},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                           "p99": float(np.percentile(lat, 99)),
-                           "kind": "one event alone (new to the context), device-resident "
-                                   "input, launch to sync"},
-            "e2e": {"value": e2e_value, "unit": "Mhits/s", "h2d_bytes_per_step": 16 * N,
-                    "d2h_bytes_per_step": 5 * N, "matches_device_path": ok},
             "gpu_launches": launches,
-            "roofline": roofline,
-            "cpu_baseline": cpu,
             "clocks": clk,
+            "tuning": tuning,
             "configs": extra,
             "served": srv,
-            "tuning": tuning,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "batched_frontier_expansion": frontier,
+            "per_event": per_event,
+            "latency_ms": latency,
+            "summary": summary,
         }))
     if dist:
         dist.destroy_process_group()

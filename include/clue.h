@@ -90,6 +90,15 @@ typedef struct clue_opts {
     int64_t max_scratch_bytes; /* 0 = no limit; otherwise a run whose scratch
                                   would exceed it fails with CLUE_ERR_OOM before
                                   any allocation (memory budgets, tests) */
+    int32_t walk_limit;  /* most steps the device may take to pass an id down one
+                            hit's chain of nearest-highers (Algorithm 3's
+                            expansion): a bounded walk of min(64, walk_limit)
+                            steps, then pointer-jumping rounds (each at least
+                            doubles the distance covered, so a chain of depth D
+                            needs about log2(D / 64) + 1).  0 = no limit beyond
+                            the 40 rounds that cover any chain.  A hit whose chain
+                            needs more gets -1 and the next clue_sync returns
+                            CLUE_ERR_TIMEOUT (the device never waits unbounded) */
 } clue_opts;
 
 #define CLUE_CHI_FLAT 0

@@ -39,7 +39,7 @@ class ClueOpts(ctypes.Structure):
                 ("block_size", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("expand", ctypes.c_int32),
                 ("chi", ctypes.c_int32), ("chi_param", ctypes.c_float),
-                ("max_scratch_bytes", ctypes.c_int64)]
+                ("max_scratch_bytes", ctypes.c_int64), ("walk_limit", ctypes.c_int32)]
 
 
 CLUE_EXPAND_FRONTIER, CLUE_EXPAND_CHASE = 0, 1
@@ -211,7 +211,7 @@ STAGE_OF = {"fill_layers": "grid_fill", "scan_segs": "grid_fill", "fill_place": 
             "fill_canon": "grid_fill", "rho": "rho",
             "nh_delta": "nh_delta",
             "scan_hits": "decide_followers", "link": "decide_followers", "assign": "expand",
-            "expand_level": "expand", "complete": "expand"}
+            "expand_level": "expand", "complete": "expand", "jump": "expand"}
 
 
 def clue_last_launch_count(ctx) -> int:
@@ -267,7 +267,7 @@ class Clusterer:
                  max_layers: int = 128, bin_size: float = 0.0, block_size: int = 0,
                  use_graphs: bool = True, expand: int = CLUE_EXPAND_CHASE,
                  chi: int = CLUE_CHI_FLAT, chi_param: float = 0.0,
-                 max_scratch_bytes: int = 0):
+                 max_scratch_bytes: int = 0, walk_limit: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -284,6 +284,7 @@ class Clusterer:
         o.chi = int(chi)
         o.chi_param = float(chi_param)
         o.max_scratch_bytes = int(max_scratch_bytes)
+        o.walk_limit = int(walk_limit)
         self.max_layers = max_layers
         self.ctx = clue_create(o)
         self._last_n = 0

@@ -87,17 +87,74 @@ __device__ __forceinline__ void link_stage(const Buffers &b, const Params &) {
     }
 }
 
-// Chase mode (CLUE_EXPAND_CHASE): ids in one pass, with no follower lists and
-// no id read that another thread writes.  Every hit walks its chain of codes
-// (a follower's code is its nearest-higher) up to the first hit that is not a
-// follower, and takes that hit's id: a seed's rank among its event's seeds
-// (from the seed bits), or -1 at an outlier or at a hit with no nearest-higher
-// -- the closed form "a follower inherits the id of its nearest-higher" of
-// Algorithm 3's expansion.  A seed's chain is the seed itself.  Chains are
-// finite because rho rises strictly along them; the walk is still bounded by
-// N steps.
-__device__ __forceinline__ void assign_stage(const Buffers &b) {
+// Pending hits of a bounded id walk (chase mode's first pass, the frontier's
+// completion pass): each stores an unresolved ancestor in jlink and joins the
+// pending list (one atomic per warp).  `mask` holds the lanes that call.
+__device__ __forceinline__ void pend_hit(const Buffers &b, unsigned mask, bool pend, int g,
+                                         int anc) {
+    const unsigned pm = __ballot_sync(mask, pend);
+    if (!pm) return;
+    const int leader = __ffs(pm) - 1;
+    int base = 0;
+    if (lane_id() == leader) base = atomicAdd(&b.ctrl->npend, __popc(pm));
+    base = __shfl_sync(mask, base, leader);
+    if (pend) {
+        b.jlink[g] = anc;
+        b.jlist[base + __popc(pm & lanemask_lt())] = g;
+    }
+}
+
+// Pointer jumping over the pending hits, by one CTA: in every round each
+// pending hit g looks at its link j = jlink[g]; if j's id is final, g takes it,
+// else g's link moves to j's link, j's ancestor.  Links only move up their
+// chain (an ancestor of an ancestor), so updates in place are safe, and every
+// round at least doubles the distance each link spans: a chain of depth D
+// needs about log2(D / CHASE_STEPS) + 1 rounds, at most JUMP_ROUNDS_MAX.  At
+// most `rounds` rounds run; hits still pending then get -1 and raise
+// ERRBIT_TIMEOUT.  Run by one CTA (k_jump) after the walk kernel.
+__device__ __forceinline__ void jump_rounds(const Buffers &b, int np, int rounds) {
+    __shared__ int s_more;
+    rounds = min(rounds, JUMP_ROUNDS_MAX);
+    for (int r = 0;; ++r) {
+        if (threadIdx.x == 0) s_more = 0;
+        __syncthreads();
+        const bool last = r >= rounds;
+        for (int k = threadIdx.x; k < np; k += blockDim.x) {
+            const int g = __ldcg(&b.jlist[k]);
+            if (__ldcg(&b.cid[g]) != PENDING) continue;
+            if (last) {  // out of rounds: the walk gives up on this hit
+                b.cid[g] = -1;
+                atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
+                continue;
+            }
+            const int j = __ldcg(&b.jlink[g]);
+            const int cj = __ldcg(&b.cid[j]);
+            if (cj != PENDING) {
+                b.cid[g] = cj;
+            } else {
+                b.jlink[g] = __ldcg(&b.jlink[j]);
+                s_more = 1;
+            }
+        }
+        __syncthreads();
+        if (last || !s_more) break;
+    }
+}
+
+// Chase mode (CLUE_EXPAND_CHASE): ids with no follower lists.  Every hit walks
+// its chain of codes (a follower's code is its nearest-higher) up to the first
+// hit that is not a follower, and takes that hit's id: a seed's rank among its
+// event's seeds (from the seed bits), or -1 at an outlier or at a hit with no
+// nearest-higher -- the closed form "a follower inherits the id of its
+// nearest-higher" of Algorithm 3's expansion.  A seed's chain is the seed
+// itself.  Chains are finite because rho rises strictly along them.  The walk
+// takes at most min(CHASE_STEPS, walk limit) steps; a hit whose chain is
+// longer stays pending and is finished by pointer jumping (jump_rounds, the
+// next kernel) with the rest of the limit, so no chain costs more than
+// O(log depth) rounds.
+__device__ __forceinline__ void assign_stage(const Buffers &b, const Params &p) {
     constexpr int U = 4;  // hits in flight per thread: their walks overlap
+    const int kmax = min(CHASE_STEPS, p.walk_limit);
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
         const int ebase = seed_rank(b, b.events[tl.event].hit_off);
@@ -121,9 +178,8 @@ __device__ __forceinline__ void assign_stage(const Buffers &b) {
                 cn[u] = kn < tl.len ? b.code[tl.start + kn] : CODE_NOISE;
                 if (act[u]) b.is_seed[v[u]] = c[u] == CODE_SEED;
             }
-            int64_t steps = 0;
             bool any = true;
-            while (any && steps <= b.N) {
+            for (int steps = 0; any && steps < kmax; ++steps) {
                 any = false;
 #pragma unroll
                 for (int u = 0; u < U; ++u)
@@ -132,18 +188,17 @@ __device__ __forceinline__ void assign_stage(const Buffers &b) {
                         c[u] = b.code[v[u]];
                         any = true;
                     }
-                ++steps;
             }
+            const unsigned mask = __activemask();
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (!act[u]) continue;
+                const int g = tl.start + k0 + u * (int)blockDim.x;
+                const bool pend = act[u] && c[u] >= 0;  // chain longer than the walk
                 int id = -1;
-                if (c[u] == CODE_SEED) {
-                    id = seed_rank(b, v[u]) - ebase;
-                } else if (c[u] >= 0) {
-                    atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
-                }
-                b.cid[tl.start + k0 + u * (int)blockDim.x] = id;
+                if (c[u] == CODE_SEED) id = seed_rank(b, v[u]) - ebase;
+                if (pend) id = PENDING;
+                if (act[u]) b.cid[g] = id;
+                pend_hit(b, mask, pend, g, c[u]);
             }
         }
     }

@@ -99,6 +99,7 @@ struct clue_ctx {
     Ctrl *d_ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;
     float bin_scale[NCLASS];
+    int tile_len[NCLASS];   // hits per tile (one CTA of every per-tile kernel) per class
     int block_density = 0;  // threads per CTA of rho / nh (one CTA per tile); 0: by run size
     bool profiling = false;
     // ring of event sets: profiled run r stamps set r % NPSETS
@@ -162,6 +163,7 @@ Params make_params(const clue_ctx *ctx, float dc, float rhoc, float delta_c, flo
     const float sp = ctx->opts.chi_param;
     p.chi_inv = p.chi == CLUE_CHI_GAUSSIAN ? 1.0f / (2.0f * (sp * sp))
               : p.chi == CLUE_CHI_EXPONENTIAL ? 1.0f / sp : 1.0f;
+    p.walk_limit = ctx->opts.walk_limit > 0 ? ctx->opts.walk_limit : INT_MAX;
     return p;
 }
 
@@ -207,9 +209,10 @@ int build_plan(clue_ctx *ctx, const int64_t *offsets, int32_t E, float dc, Plan 
             return CLUE_ERR_ARG;
         }
         d.tile0 = (int32_t)plan.tiles.size();
-        for (int64_t t = 0; t < n; t += TILE)
+        const int64_t tlen = ctx->tile_len[class_of(n)];
+        for (int64_t t = 0; t < n; t += tlen)
             plan.tiles.push_back(Tile{(int32_t)(offsets[e] + t),
-                                      (int32_t)std::min<int64_t>(TILE, n - t), e, 0});
+                                      (int32_t)std::min<int64_t>(tlen, n - t), e, 0});
         d.ntiles = (int32_t)plan.tiles.size() - d.tile0;
     }
     plan.N = offsets[E];
@@ -252,7 +255,8 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t E, int64_t
     // the fill) the per-hit records delta^2, nh of the nh step (8 bytes each)
     b.rec = (float4 *)take(n * 16);
     b.hr = (float2 *)b.rec;
-    b.spr = (float4 *)take(n * 16);
+    b.rho = (float *)take(n * 4);
+    b.front_b = (int32_t *)take(n * 4);  // the second expansion frontier
     b.code = b.key;  // the cell of each hit is dead once the cells are sorted
     b.cell16 = (unsigned short *)b.key;
     b.fcount = (int32_t *)take(n * 4);
@@ -262,9 +266,10 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t E, int64_t
     b.fol = (int32_t *)take(n * 4);
     b.seed_list = (int32_t *)take(n * 4);
     b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
-    b.front_a = b.perm;  // the frontiers reuse the grid fill's scratch
-    b.front_b = b.tmp;
-    b.sid = b.tmp;  // the sorted ids are dead once rho has copied them
+    b.front_a = b.perm;  // the first frontier reuses the grid fill's scratch
+    b.jlink = b.fcount;  // pointer jumping: after the scan (frontier) or unused (chase)
+    b.jlist = b.seed_list;
+    b.sid = b.tmp;
     const int64_t parts =
         std::max({scan_partials_needed(N), scan_partials_needed(C), scan_partials_needed(ntb)}) + 1;
     b.scan_partials = take((size_t)parts * 8);
@@ -358,14 +363,13 @@ int upload_tables_async(clue_ctx *ctx, const Plan &plan) {
 }
 
 // The density kernels run one CTA per tile.  Unless the options or the
-// tuning table fix their block size, a run with enough tiles to give every SM
-// eight CTAs uses 128 threads (eight hits per thread; finer CTAs balance the
-// uneven windows better), one with at least a tile per SM 256, and a smaller
+// tuning table fix their block size, a run with at least a tile per SM uses
+// 256 threads (four CTAs per SM, as their shared memory allows), a smaller
 // one 1024 (one hit per thread: its few tiles' hits all in flight at once).
 LaunchCfg make_cfg(const clue_ctx *ctx, int64_t ntiles) {
     LaunchCfg c;
     c.block_fill = 256;
-    const int automatic = ntiles >= 8LL * ctx->num_sms ? 128 : ntiles >= ctx->num_sms ? 256 : 1024;
+    const int automatic = ntiles >= ctx->num_sms ? 256 : 1024;
     c.block_density = ctx->opts.block_size > 0 ? ctx->opts.block_size
                     : ctx->block_density > 0   ? ctx->block_density
                                                : automatic;
@@ -433,9 +437,11 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(launch_scan_hits(b, p, cfg, s, &nl));
     CK(rec("scan_hits"));
     if (p.chase) {
-        CK(launch_assign(b, cfg, s));
+        CK(launch_assign(b, p, cfg, s));
         CK(rec("assign"));
-        nl += 3;  // rho, nh (with the decision), assign
+        CK(launch_jump(b, p, s));
+        CK(rec("jump"));
+        nl += 4;  // rho, nh (with the decision), assign, jump
     } else {
         CK(launch_link(b, p, cfg, s));
         CK(rec("link"));
@@ -443,9 +449,11 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
             CK(launch_expand_level(b, cfg, level, s));
             CK(rec("expand_level"));
         }
-        CK(launch_complete(b, cfg, s));
+        CK(launch_complete(b, p, cfg, s));
         CK(rec("complete"));
-        nl += 4 + EXPAND_LEVELS;  // rho, nh, link, complete, levels
+        CK(launch_jump(b, p, s));
+        CK(rec("jump"));
+        nl += 5 + EXPAND_LEVELS;  // rho, nh, link, complete, jump, levels
     }
     *launches = nl;
     return CLUE_OK;
@@ -725,6 +733,7 @@ void clue_default_opts(clue_opts *o) {
     o->chi = CLUE_CHI_FLAT;
     o->chi_param = 0.0f;
     o->max_scratch_bytes = 0;
+    o->walk_limit = 0;
 }
 
 int clue_create(clue_ctx **out, const clue_opts *opts) {
@@ -737,7 +746,7 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
         o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0 ||
         (o.expand != CLUE_EXPAND_FRONTIER && o.expand != CLUE_EXPAND_CHASE) ||
         o.chi < CLUE_CHI_FLAT || o.chi > CLUE_CHI_EXPONENTIAL || o.max_scratch_bytes < 0 ||
-
+        o.walk_limit < 0 ||
         (o.chi != CLUE_CHI_FLAT && !(o.chi_param > 0.0f && std::isfinite(o.chi_param))))
         return CLUE_ERR_ARG;
     clue_ctx *ctx = new (std::nothrow) clue_ctx();
@@ -748,7 +757,10 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
     // or fewer for events spread over many layers (what the autotuner picks
     // on such events); the smaller the event, the sparser its layers.
     const float defaults[NCLASS] = {8.0f, 4.0f, 3.0f, 2.0f, 1.0f};
-    for (int k = 0; k < NCLASS; ++k) ctx->bin_scale[k] = defaults[k];
+    for (int k = 0; k < NCLASS; ++k) {
+        ctx->bin_scale[k] = defaults[k];
+        ctx->tile_len[k] = TILE;
+    }
     auto fail = [&](cudaError_t e, const char *what) {
         int rc = cuda_fail(ctx, e, what);
         clue_destroy(ctx);
@@ -1074,13 +1086,16 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
         return clue_sync(ctx);
     };
     const float scales[] = {0.5f, 0.75f, 1.0f, 1.5f, 2.0f, 3.0f, 4.0f, 6.0f, 8.0f, 12.0f};
-    const int blocks[] = {128, 256};
+    const int tiles[] = {256, 512, 1024};  // hits per tile: 1, 2, 4 per thread at 256 threads
+    const int blocks[] = {128, 256, 512};
     const float user_bin = ctx->opts.bin_size;
     const int user_block = ctx->opts.block_size;
     ctx->opts.bin_size = 0.0f;
     ctx->opts.block_size = 0;
     // Each size class is timed on its own events, copied into one contiguous
-    // sub-batch, so its bin size is chosen on its own time alone.
+    // sub-batch, so its choices rest on its own time alone: the bin size at
+    // the class's tile length, then the tile length (hits per CTA, so hits
+    // per thread) at that bin size, then the bin size again at that length.
     for (int k = 0; k < NCLASS && rc == CLUE_OK; ++k) {
         std::vector<int64_t> sub{0};
         for (int32_t e = 0; e < n_events; ++e) {
@@ -1104,21 +1119,42 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
             at += n;
         }
         if (rc) break;
-        float best = 1e30f, best_s = ctx->bin_scale[k];
-        for (float sc : scales) {
-            ctx->bin_scale[k] = sc;
-            float ms = 0;
-            rc = time_run(io.x, io.y, io.l, io.e, sub.data(), (int32_t)sub.size() - 1, io.cid,
-                          io.seed, &ms);
-            if (rc) break;
-            if (ms < best) {
-                best = ms;
-                best_s = sc;
+        auto time_class = [&](float *out_ms) {
+            return time_run(io.x, io.y, io.l, io.e, sub.data(), (int32_t)sub.size() - 1, io.cid,
+                            io.seed, out_ms);
+        };
+        for (int pass = 0; pass < 3 && rc == CLUE_OK; ++pass) {
+            float best = 1e30f;
+            if (pass != 1) {
+                float best_s = ctx->bin_scale[k];
+                for (float sc : scales) {
+                    ctx->bin_scale[k] = sc;
+                    float ms = 0;
+                    rc = time_class(&ms);
+                    if (rc) break;
+                    if (ms < best) {
+                        best = ms;
+                        best_s = sc;
+                    }
+                }
+                ctx->bin_scale[k] = best_s;
+            } else {
+                int best_t = ctx->tile_len[k];
+                for (int tl : tiles) {
+                    ctx->tile_len[k] = tl;
+                    float ms = 0;
+                    rc = time_class(&ms);
+                    if (rc) break;
+                    if (ms < best) {
+                        best = ms;
+                        best_t = tl;
+                    }
+                }
+                ctx->tile_len[k] = best_t;
             }
         }
-        ctx->bin_scale[k] = best_s;
     }
-    if (rc == CLUE_OK) {
+    if (rc == CLUE_OK) {  // the density kernels' block size, on the whole batch
         float best = 1e30f;
         int best_b = ctx->block_density;
         for (int bsz : blocks) {
@@ -1144,11 +1180,11 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
 
 int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap) {
     if (!ctx) return -CLUE_ERR_ARG;
-    std::string s = "# clue tuning v1: class <lo> <hi> <bin_scale>; block <threads>\n";
+    std::string s = "# clue tuning v2: class <lo> <hi> <bin_scale> <tile_hits>; block <threads>\n";
     char line[160];
     for (int k = 0; k < NCLASS; ++k) {
-        std::snprintf(line, sizeof(line), "class %" PRId64 " %" PRId64 " %.4f\n", CLASS_EDGE[k],
-                      CLASS_EDGE[k + 1], (double)ctx->bin_scale[k]);
+        std::snprintf(line, sizeof(line), "class %" PRId64 " %" PRId64 " %.4f %d\n", CLASS_EDGE[k],
+                      CLASS_EDGE[k + 1], (double)ctx->bin_scale[k], ctx->tile_len[k]);
         s += line;
     }
     std::snprintf(line, sizeof(line), "block %d\n", ctx->block_density);
@@ -1163,7 +1199,11 @@ int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap) {
 int clue_set_tuning(clue_ctx *ctx, const char *text) {
     if (!ctx || !text) return CLUE_ERR_ARG;
     float scale[NCLASS];
-    for (int k = 0; k < NCLASS; ++k) scale[k] = ctx->bin_scale[k];
+    int tlen[NCLASS];
+    for (int k = 0; k < NCLASS; ++k) {
+        scale[k] = ctx->bin_scale[k];
+        tlen[k] = ctx->tile_len[k];
+    }
     int block = ctx->block_density;
     const char *p = text;
     while (*p) {
@@ -1173,22 +1213,30 @@ int clue_set_tuning(clue_ctx *ctx, const char *text) {
         if (line.empty() || line[0] == '#') continue;
         long long lo, hi;
         float sc;
-        int bl;
+        int bl, tl = TILE;
         char tail;
-        if (std::sscanf(line.c_str(), "class %lld %lld %f %c", &lo, &hi, &sc, &tail) == 3) {
+        // "class lo hi scale [tile_hits]" (the tile length is optional: v1 text)
+        const int nf = std::sscanf(line.c_str(), "class %lld %lld %f %d %c", &lo, &hi, &sc, &tl,
+                                   &tail);
+        if (nf == 3 || nf == 4) {
             int k = -1;
             for (int i = 0; i < NCLASS; ++i)
                 if (CLASS_EDGE[i] == lo && CLASS_EDGE[i + 1] == hi) k = i;
-            if (k < 0 || !(sc >= 0.25f && sc <= 64.0f)) return CLUE_ERR_ARG;
+            if (k < 0 || !(sc >= 0.25f && sc <= 64.0f) || tl < 32 || tl > TILE || tl % 32)
+                return CLUE_ERR_ARG;
             scale[k] = sc;
+            tlen[k] = tl;
         } else if (std::sscanf(line.c_str(), "block %d %c", &bl, &tail) == 1) {
-            if (bl != 0 && (bl < 32 || bl > 256 || bl % 32)) return CLUE_ERR_ARG;  // 0: by run size
+            if (bl != 0 && (bl < 32 || bl > 1024 || bl % 32)) return CLUE_ERR_ARG;  // 0: by run size
             block = bl;
         } else {
             return CLUE_ERR_ARG;
         }
     }
-    for (int k = 0; k < NCLASS; ++k) ctx->bin_scale[k] = scale[k];
+    for (int k = 0; k < NCLASS; ++k) {
+        ctx->bin_scale[k] = scale[k];
+        ctx->tile_len[k] = tlen[k];
+    }
     ctx->block_density = block;
     drop_graphs(ctx);
     return CLUE_OK;

@@ -50,12 +50,21 @@ struct Tile {
 // than this is finished by the completion pass.
 constexpr int EXPAND_LEVELS = 12;
 
+// Steps of the bounded first pass of the id walk (chase mode's k_assign, the
+// frontier's completion pass): trees this shallow (the usual case) finish
+// there; the hits of deeper chains are finished by pointer jumping.
+constexpr int CHASE_STEPS = 64;
+// Pointer-jumping rounds: each at least doubles the distance a pending hit's
+// link spans, so 40 rounds exceed any chain of at most 2^31 hits.
+constexpr int JUMP_ROUNDS_MAX = 40;
+
 // Device control block.  `err` is sticky until clue_sync reads it; the rest
 // is zeroed at the start of every run.
 struct Ctrl {
     unsigned err;        // ERRBIT_* raised by any kernel
     unsigned overflow;   // the expansion left nodes for the completion pass
     int32_t fsize[3];    // frontier sizes, rotating over the expansion levels
+    int32_t npend;       // hits the bounded walk left pending (pointer jumping)
 };
 
 // Runtime parameters of one run (all events share them).
@@ -71,6 +80,7 @@ struct Params {
     int32_t chase;   // 1: expansion by chasing nh chains (no follower lists)
     int32_t chi;     // density kernel: 0 flat, 1 Gaussian, 2 exponential
     float chi_inv;   // 1 / (2 s^2) (Gaussian) or 1 / s (exponential)
+    int32_t walk_limit;  // most steps of a hit's id walk: bounded walk + jump rounds
 };
 
 // Device pointers of one run, carved from the scratch arena.
@@ -113,14 +123,15 @@ struct Buffers {
                              //     sort; aliases key)
     int64_t nseg;        // events x layers, or 0: the direct sort
     int32_t max_cells;   // most cells in one layer (the cell sort's shared memory)
-    int32_t *tmp;        // [N] the sorted ids (sid), then the second expansion frontier
+    int32_t *tmp;        // [N] the sorted ids (sid)
     float4 *sp;          // [N] hits sorted by (event, layer, cell): x, y, w, id (int
                          //     bits), or for an event on the flat kernel's fixed point
                          //     x, y and the 64-bit integer weight (two words)
-    int32_t *sid;        // [N] hit id by sorted position (aliases tmp)
+    int32_t *sid;        // [N] hit id by sorted position (aliases tmp; kept for the
+                         //     nh step and the intermediates export)
     int32_t *lay_s;      // [N] layer in sorted order
     // density
-    float4 *spr;         // [N] sorted order: x, y, rho, id (written by the rho step)
+    float *rho;          // [N] rho by sorted position (written by the rho step)
     float2 *hr;          // [N] by sorted position: delta^2, nh (int bits: batch index
                          //     or -1), read only by the intermediates export
     // decision / expansion
@@ -134,8 +145,12 @@ struct Buffers {
     int32_t *sword;      // [N / 32 + 2] exclusive scan of the words' seed counts
     int32_t *fol;        // [N] follower lists (CSR by nh)
     int32_t *seed_list;  // [N] seeds by global seed rank
-    int32_t *front_a;    // [N] expansion frontiers (alias perm / tmp, free after S1)
+    int32_t *front_a;    // [N] expansion frontiers (front_a aliases perm, free after S1)
     int32_t *front_b;
+    int32_t *jlink;      // [N] pointer jumping: an unresolved ancestor of each pending
+                         //     hit (aliases fcount: dead once the scan has read it)
+    int32_t *jlist;      // [N] the pending hits (aliases seed_list: dead after the
+                         //     frontier's levels, unused in chase mode)
     // scan scratch
     void *scan_partials; // [nblocks + 1] block sums
     int64_t scan_partials_cap;
@@ -167,10 +182,11 @@ cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cud
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s,
                              int *launches);
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_assign(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_assign(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);  // all levels
 cudaError_t launch_expand_level(const Buffers &b, const LaunchCfg &c, int level, cudaStream_t s);
-cudaError_t launch_complete(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_complete(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_jump(const Buffers &b, const Params &p, cudaStream_t s);
 cudaError_t launch_export(const Buffers &b, const LaunchCfg &c, float *rho, float *delta,
                           int32_t *nh, cudaStream_t s);
 

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -39,7 +40,7 @@ constexpr size_t STATIC_BYTES =
     al(NB * 4) /*key*/ + al(NB * 4) /*rank*/ + al(CB * 4) /*count*/ + al((CB + 1) * 4) /*cell_start*/ +
     al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ +
     al(NB * 16) /*sp*/ + al(NB * 4) /*lay_s*/ +
-    al(NB * 16) /*rec = hr*/ + al(NB * 16) /*spr*/ +
+    al(NB * 16) /*rec = hr*/ + al(NB * 4) /*rho*/ + al(NB * 4) /*front_b*/ +
     al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
     al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/ + al(8) /*wexp*/;
 
@@ -148,7 +149,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.lay_s = (int32_t *)take(NB * 4);
     b.rec = (float4 *)take(NB * 16);
     b.hr = (float2 *)b.rec;
-    b.spr = (float4 *)take(NB * 16);
+    b.rho = (float *)take(NB * 4);
+    b.front_b = (int32_t *)take(NB * 4);
     b.code = b.key;
     b.fcount = (int32_t *)take(NB * 4);
     b.hs = (unsigned long long *)take((NB + 1) * 8);
@@ -158,7 +160,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.seed_list = (int32_t *)take(NB * 4);
     b.frank = b.rank;  // the fill's ranks are dead once the cells are sorted
     b.front_a = b.perm;
-    b.front_b = b.tmp;
+    b.jlink = b.fcount;
+    b.jlist = b.seed_list;
     b.sid = b.tmp;
     b.scan_partials = take((size_t)STATIC_PARTS * 8);
     b.scan_partials_cap = STATIC_PARTS;
@@ -212,6 +215,7 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     prm.chase = 0;
     prm.chi = 0;
     prm.chi_inv = 1.0f;
+    prm.walk_limit = INT_MAX;
     LaunchCfg cfg;
     cfg.block_fill = 256;
     cfg.block_density = 128;
@@ -242,7 +246,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     SCK(launch_scan_hits(b, prm, cfg, s, &nl));
     SCK(launch_link(b, prm, cfg, s));
     SCK(launch_expand(b, cfg, s));
-    SCK(launch_complete(b, cfg, s));
+    SCK(launch_complete(b, prm, cfg, s));
+    SCK(launch_jump(b, prm, s));
     Ctrl h{};
     SCK(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     SCK(cudaStreamSynchronize(s));

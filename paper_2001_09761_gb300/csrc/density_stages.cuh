@@ -1,11 +1,10 @@
 // Steps S2 and S3: local density rho (Eq. 3, Algorithm 1) and nearest-higher
-// nh / separation delta (Eq. 4, Algorithm 2): the stage bodies, which the
-// kernels in k_density.cu wrap.
+// nh / separation delta (Eq. 4, Algorithm 2): the shared arithmetic and the
+// per-hit forms, which the tile kernels in density_tile.cuh use.
 //
-// One thread per hit in grid (sorted) order, so a warp covers neighbouring
-// cells and its window loads hit the same lines.  The window of Eq. 1 is the
-// set of bins met by [x +- R] x [y +- R]; bins of one grid row are adjacent in
-// the sorted array, so a window row is one contiguous run.  Each sorted hit is
+// Hits are read in grid (sorted) order.  The window of Eq. 1 is the set of
+// bins met by [x +- R] x [y +- R]; bins of one grid row are adjacent in the
+// sorted array, so a window row is one contiguous run.  Each sorted hit is
 // one float4 (x, y, w, id), so a candidate costs one 16-byte load.
 //
 // rho_i is the exact sum over N_dc(i) of the terms chi(d_ij) w_j (flat chi =
@@ -22,7 +21,7 @@
 // weights span few enough binary orders (the fill records each event's
 // exponent range) is summed in 64-bit fixed point instead: every weight is an
 // integer multiple of the event's smallest weight's last place, so the sum is
-// an exact integer, rounded once at the end (rho_stage below).
+// an exact integer, rounded once at the end.
 #pragma once
 
 #include <climits>
@@ -168,158 +167,124 @@ __device__ __noinline__ float rho_wide(const Buffers &b, int64_t plane, int nbx,
 // the result is normal, which g >= 24 ensures (a nonzero sum is at least
 // 2^(g - 150)); an overflow gives inf as the correctly rounded sum would.
 // Windows past the bound go to the integer accumulator.
+
+// The running state of one hit's TwoSum density (see above).
+struct TwoSumAcc {
+    float s = 0.0f, c = 0.0f, smax = 0.0f;
+    unsigned tmin = 0x7f800000u;  // bits of the smallest nonzero |term|
+    int m = 0;
+    __device__ __forceinline__ void add(float tv, bool near) {
+        const float s1 = __fadd_rn(s, tv);  // TwoSum: s + tv = s1 + err exactly
+        const float bb = __fsub_rn(s1, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(tv, bb));
+        s = s1;
+        c = __fadd_rn(c, err);
+        smax = fmaxf(smax, fabsf(s1));
+        const unsigned ta = __float_as_uint(tv) & 0x7fffffffu;
+        tmin = ta ? min(tmin, ta) : tmin;
+        m += near;
+    }
+    // Whether s + c is the exact sum (else the caller takes the integer
+    // accumulator).
+    __device__ __forceinline__ bool exact() const {
+        const int g = max((int)(tmin >> 23), 1);  // 2^(g - 150): last place
+        const int E = max((int)(__float_as_uint(smax) >> 23), 1);
+        const int L = 32 - __clz(m);
+        return E < 255 && L + E - 25 <= g;
+    }
+};
+
+// rho of one sorted hit q by a walk over its window in global memory (one
+// thread per hit): the general form, for tiles the staged forms do not take.
 template <int CHI>
-__device__ __forceinline__ void rho_stage(const Buffers &b, const Params &p) {
-    const float4 *__restrict__ sp = b.sp;
-    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-        const Tile tl = b.tiles[t];
-        const EventDesc ev = b.events[tl.event];
-        const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
-        // the fill stored this event's records in fixed point or not (uniform)
-        const FixedW fw = fixed_weights(b.wexp + 2 * tl.event, CHI);
-        if (CHI == 0 && fw.on) {
-            // the next hit's record and layer are loaded while this one's
-            // window is scanned
-            float4 me_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            int lay_next = 0;
-            if ((int)threadIdx.x < tl.len) {
-                me_next = sp[tl.start + threadIdx.x];
-                lay_next = b.lay_s[tl.start + threadIdx.x];
+__device__ __forceinline__ float rho_of_hit(const Buffers &b, const Params &p,
+                                            const EventDesc &ev, const FixedW &fw, float4 me,
+                                            int lay) {
+    const int64_t plane = ev.cell_off + (int64_t)lay * ev.nbx * ev.nby;
+    const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
+    if (CHI == 0 && fw.on) {
+        long long acc = 0;
+        unsigned T = 0;
+        for (int by = w.ly; by <= w.hy; ++by) {
+            const int64_t row = plane + (int64_t)by * ev.nbx;
+            const int u0 = b.cell_start[row + w.lx], e = b.cell_start[row + w.hx + 1];
+            T += (unsigned)(e - u0);
+            for (int u = u0; u < e; ++u) {  // branch-free body
+                const float4 h = b.sp[u];
+                const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                acc += d2 < p.dc2 ? fixed_weight_of(h) : 0ll;
             }
-            for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-                const int q = tl.start + k;
-                const float4 me = me_next;
-                const int lay = lay_next;
-                if (k + (int)blockDim.x < tl.len) {
-                    me_next = sp[q + blockDim.x];
-                    lay_next = b.lay_s[q + blockDim.x];
-                }
-                const int64_t plane = ev.cell_off + (int64_t)lay * nbxy;
-                const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
-                long long acc = 0;
-                unsigned T = 0;
-                for (int by = w.ly; by <= w.hy; ++by) {
-                    const int64_t row = plane + (int64_t)by * ev.nbx;
-                    const int u0 = b.cell_start[row + w.lx], e = b.cell_start[row + w.hx + 1];
-                    T += (unsigned)(e - u0);
-                    for (int u = u0; u < e; ++u) {  // branch-free body
-                        const float4 h = sp[u];
-                        const float d2 = sq_dist(me.x, me.y, h.x, h.y);
-                        acc += d2 < p.dc2 ? fixed_weight_of(h) : 0ll;
-                    }
-                }
-                const float r = 32 - __clz(T) <= fw.budget
-                                    ? __fmul_rn(__ll2float_rn(acc), fw.unit)
-                                    : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv,
-                                                    fw.unit);
-                b.spr[q] = make_float4(me.x, me.y, r, __int_as_float(b.sid[q]));  // for the nh step
-            }
-            continue;
         }
-        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-            const int q = tl.start + k;
-            const float4 me = sp[q];
-            const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
-            const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
-            float s = 0.0f, c = 0.0f, smax = 0.0f;
-            unsigned tmin = 0x7f800000u;  // bits of the smallest nonzero |term|
-            int m = 0;
-            for (int by = w.ly; by <= w.hy; ++by) {
-                const int64_t row = plane + (int64_t)by * ev.nbx;
-                const int e = b.cell_start[row + w.hx + 1];
-                for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
-                    const float4 h = sp[u];
-                    const float d2 = sq_dist(me.x, me.y, h.x, h.y);
-                    const bool near = d2 < p.dc2;
-                    const float tv = near ? term_of<CHI>(d2, h.z, p.chi_inv) : 0.0f;
-                    // TwoSum: s + tv = s1 + err exactly
-                    const float s1 = __fadd_rn(s, tv);
-                    const float bb = __fsub_rn(s1, s);
-                    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(tv, bb));
-                    s = s1;
-                    c = __fadd_rn(c, err);
-                    smax = fmaxf(smax, fabsf(s1));
-                    const unsigned ta = __float_as_uint(tv) & 0x7fffffffu;
-                    tmin = ta ? min(tmin, ta) : tmin;
-                    m += near;
-                }
-            }
-            const int g = max((int)(tmin >> 23), 1);             // 2^(g - 150): last place
-            const int E = max((int)(__float_as_uint(smax) >> 23), 1);
-            const int L = 32 - __clz(m);
-            const bool exact = E < 255 && L + E - 25 <= g;
-            const float r = exact ? __fadd_rn(s, c)
-                                  : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv,
-                                                  0.0f);
-            b.spr[q] = make_float4(me.x, me.y, r, __int_as_float(b.sid[q]));  // for the nh step
+        return 32 - __clz(T) <= fw.budget
+                   ? __fmul_rn(__ll2float_rn(acc), fw.unit)
+                   : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv, fw.unit);
+    }
+    TwoSumAcc a;
+    for (int by = w.ly; by <= w.hy; ++by) {
+        const int64_t row = plane + (int64_t)by * ev.nbx;
+        const int e = b.cell_start[row + w.hx + 1];
+        for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
+            const float4 h = b.sp[u];
+            const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+            const bool near = d2 < p.dc2;
+            a.add(near ? term_of<CHI>(d2, h.z, p.chi_inv) : 0.0f, near);
         }
     }
+    return a.exact() ? __fadd_rn(a.s, a.c)
+                     : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv, 0.0f);
 }
 
-// nh_i: over the window of radius d_m, the (d2, j)-lexicographic minimum among
-// hits with d2 < d_m^2 and rho_j > rho_i (the minimum is order-free).  The
-// same thread takes the seed / outlier decision (Sec. 2.2), which needs only
-// this hit's rho, delta and nh, and stores one 4-byte code by hit (the
-// scattered store this step cannot avoid); delta^2 and nh also go, in sorted
-// order (coalesced), to an 8-byte record the intermediates export reads (rho
-// stays in the rho step's sorted records).
-__device__ __forceinline__ void nh_stage(const Buffers &b, const Params &p) {
-    const float4 *__restrict__ sp = b.spr;  // x, y, rho, id
-    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-        const Tile tl = b.tiles[t];
-        const EventDesc ev = b.events[tl.event];
-        const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
-        // the next hit's record and layer are loaded while this one's window
-        // is scanned
-        float4 me_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        int lay_next = 0;
-        if ((int)threadIdx.x < tl.len) {
-            me_next = sp[tl.start + threadIdx.x];
-            lay_next = b.lay_s[tl.start + threadIdx.x];
-        }
-        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-            const int q = tl.start + k;
-            const float4 me = me_next;
-            const int lay = lay_next;
-            if (k + (int)blockDim.x < tl.len) {
-                me_next = sp[q + blockDim.x];
-                lay_next = b.lay_s[q + blockDim.x];
-            }
-            const float ri = me.z;
-            const int64_t plane = ev.cell_off + (int64_t)lay * nbxy;
-            const Window w = window_of(me.x, me.y, p.rwin_nh, ev);
-            // (d2, j) packed as one unsigned key: d2 >= 0, so its float bits
-            // order like its value; starting at (bits(d_m^2), 0) also folds in
-            // the strict test d2 < d_m^2
-            const unsigned long long none = (unsigned long long)__float_as_uint(p.dm2) << 32;
-            unsigned long long best = none;
-            for (int by = w.ly; by <= w.hy; ++by) {
-                const int64_t row = plane + (int64_t)by * ev.nbx;
-                const int e = b.cell_start[row + w.hx + 1];
-                for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
-                    const float4 h = sp[u];
-                    const float d2 = sq_dist(me.x, me.y, h.x, h.y);
-                    const unsigned long long k =
-                        ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)id_of(h);
-                    best = (h.z > ri && k < best) ? k : best;
-                }
-            }
-            const bool found = best != none;
-            const float d2v = found ? __uint_as_float((unsigned)(best >> 32))
-                                    : __int_as_float(0x7f800000);  // +inf (Eq. 4)
-            const int nhj = found ? (int)(unsigned)best : -1;
-            b.hr[q] = make_float2(d2v, __int_as_float(nhj));
-            // the decision of Sec. 2.2 needs only this hit's rho, delta and nh:
-            // seed, outlier, or a follower of nh (Algorithm 3), stored by hit
-            const bool seed = (ri > p.rhoc) && (d2v > p.dcs2);
-            const bool outl = (ri < p.rhoc) && (d2v > p.dos2);
-            const int code = seed ? CODE_SEED : outl ? CODE_OUTLIER : (nhj >= 0 ? nhj : CODE_NOISE);
-            const int g = id_of(me);
-            b.code[g] = code;
-            if (p.chase && seed) atomicOr(&b.sbits[g >> 5], 1u << (g & 31));
-            if (!p.chase && code >= 0) b.frank[g] = atomicAdd(&b.fcount[code], 1);
+// The (d2, j) key that starts an nh search: d2 >= 0, so its float bits order
+// like its value, and starting at (bits(d_m^2), 0) folds in the strict test
+// d2 < d_m^2.
+__device__ __forceinline__ unsigned long long nh_none(const Params &p) {
+    return (unsigned long long)__float_as_uint(p.dm2) << 32;
+}
+
+__device__ __forceinline__ unsigned long long nh_key(float d2, int j) {
+    return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
+}
+
+// nh_i by a walk over i's window in global memory (one thread per hit): over
+// the window of radius d_m, the (d2, j)-lexicographic minimum among hits with
+// d2 < d_m^2 and rho_j > rho_i (the minimum is order-free).
+__device__ __forceinline__ unsigned long long nh_of_hit(const Buffers &b, const Params &p,
+                                                       const EventDesc &ev, float xi, float yi,
+                                                       float ri, int lay) {
+    const int64_t plane = ev.cell_off + (int64_t)lay * ev.nbx * ev.nby;
+    const Window w = window_of(xi, yi, p.rwin_nh, ev);
+    unsigned long long best = nh_none(p);
+    for (int by = w.ly; by <= w.hy; ++by) {
+        const int64_t row = plane + (int64_t)by * ev.nbx;
+        const int e = b.cell_start[row + w.hx + 1];
+        for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
+            const float4 h = b.sp[u];
+            const float d2 = sq_dist(xi, yi, h.x, h.y);
+            const unsigned long long k = nh_key(d2, b.sid[u]);
+            best = (b.rho[u] > ri && k < best) ? k : best;
         }
     }
+    return best;
+}
+
+// The seed / outlier decision of Sec. 2.2 for sorted hit q (hit g), which
+// needs only its rho, delta and nh: seed, outlier, or a follower of nh
+// (Algorithm 3), stored as one code by hit (the scattered store this step
+// cannot avoid); delta^2 and nh also go, in sorted order (coalesced), to an
+// 8-byte record the intermediates export reads.
+__device__ __forceinline__ void nh_store(const Buffers &b, const Params &p, int64_t q, int g,
+                                         float ri, unsigned long long best) {
+    const bool found = best != nh_none(p);
+    const float d2v = found ? __uint_as_float((unsigned)(best >> 32))
+                            : __int_as_float(0x7f800000);  // +inf (Eq. 4)
+    const int nhj = found ? (int)(unsigned)best : -1;
+    b.hr[q] = make_float2(d2v, __int_as_float(nhj));
+    const bool seed = (ri > p.rhoc) && (d2v > p.dcs2);
+    const bool outl = (ri < p.rhoc) && (d2v > p.dos2);
+    const int code = seed ? CODE_SEED : outl ? CODE_OUTLIER : (nhj >= 0 ? nhj : CODE_NOISE);
+    b.code[g] = code;
+    if (p.chase && seed) atomicOr(&b.sbits[g >> 5], 1u << (g & 31));
+    if (!p.chase && code >= 0) b.frank[g] = atomicAdd(&b.fcount[code], 1);
 }
 
 }  // namespace clue

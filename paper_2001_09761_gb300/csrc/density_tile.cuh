@@ -1,0 +1,396 @@
+// Steps S2 and S3 tile by tile: rho (Eq. 3, Algorithm 1) and nh / delta with
+// the seed / outlier decision (Eq. 4, Algorithm 2, Sec. 2.2), one CTA per tile
+// of sorted hits, with the tile's candidates staged in shared memory.
+//
+// One thread per hit in grid order leaves half a warp idle: the windows of
+// neighbouring hits hold from one to tens of candidates, and a warp runs as
+// long as its longest window row by row.  Here a CTA first finds every window
+// of its tile (the runs of sorted positions of its 1 to 3 grid rows) and the
+// band of sorted positions all of them lie in, then
+//
+//  * sorted form (the band fits in shared memory, windows of at most DT_ROWS
+//    rows): the band is staged once, the tile's hits are ordered by
+//    descending candidate count (a counting sort in shared memory), so the
+//    32 lanes of a warp take hits with near-equal windows, and each lane walks
+//    its window's runs as one flat loop (no per-row reconvergence);
+//  * warp form (rho with the fixed point, and nh, on tiles whose windows
+//    average DENSE_MEAN candidates or more: dense hotspots): a warp takes one
+//    hit at a time and its lanes stride over the window's runs (coalesced
+//    loads from global memory), with a warp reduction of the integer sum or
+//    of the (d2, j) key;
+//  * per-hit form otherwise (windows of more rows, bands beyond the staging
+//    capacity): one thread per hit walks its window in global memory.
+//
+// Every form computes the same function of the neighbour sets (the exact
+// density, the lexicographic minimum), so the form, the order of the hits and
+// the order of the candidates never change a result.
+#pragma once
+
+#include "density_stages.cuh"
+
+namespace clue {
+
+constexpr int BAND_CAP = 1792;   // staged candidates per tile (16 bytes each)
+constexpr int DT_ROWS = 3;       // window rows the sorted form walks
+constexpr int DT_BUCKETS = 64;   // work classes of the counting sort (64+ share one)
+constexpr int DENSE_MEAN = 96;   // mean window population that takes the warp form
+constexpr int DT_OUT = 1 << 14;  // window starts further than this from the tile
+
+// One hit's window for the sorted form: per row (up to DT_ROWS) the start
+// relative to the tile start (16 bits) and the length (16 bits), and the
+// candidate count; all in one 16-byte word.
+__device__ __forceinline__ unsigned pack_row(int rel, int len) {
+    return (unsigned)(unsigned short)(short)max(-DT_OUT, min(DT_OUT, rel)) |
+           ((unsigned)min(len, 65535) << 16);
+}
+__device__ __forceinline__ int row_start(unsigned w) { return (int)(short)(w & 0xffffu); }
+__device__ __forceinline__ int row_len(unsigned w) { return (int)(w >> 16); }
+
+// Per-tile shared state: 18 KB, plus the staged band (28 KB).
+struct DensityShared {
+    uint4 win[TILE];                   // windows (pack_row x 3, candidate count)
+    unsigned short perm[TILE];         // the tile's hits by descending window population
+    int hist[DT_BUCKETS];
+    int lo, hi, rows;                  // the band [lo, hi) (relative) and the most rows
+    unsigned long long tsum;           // candidates over the tile's windows
+};
+
+// The tile's windows of radius parameter `dr` into sh.win (rows past DT_ROWS
+// and starts past DT_OUT are flagged through sh.rows / the band, which then
+// disqualify the sorted form), the band and the work histogram.  A thread
+// takes the tile's hits k = threadIdx.x + u * blockDim.x, u < U, and issues
+// each round of loads (records and layers, then every window row's bounds)
+// for all of them before it waits on any.
+template <int U>
+__device__ __forceinline__ void tile_windows(const Buffers &b, const Tile &tl,
+                                             const EventDesc &ev, float dr,
+                                             DensityShared &sh) {
+    if (threadIdx.x < DT_BUCKETS) sh.hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        sh.lo = INT_MAX;
+        sh.hi = INT_MIN;
+        sh.rows = 0;
+        sh.tsum = 0ull;
+    }
+    __syncthreads();
+    const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
+    int lo = INT_MAX, hi = INT_MIN, rows = 0;
+    unsigned long long tsum = 0ull;
+    for (int k0 = threadIdx.x; k0 < tl.len; k0 += U * blockDim.x) {
+        float4 me[U];
+        int lay[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * blockDim.x;
+            const int q = tl.start + (k < tl.len ? k : 0);
+            me[u] = b.sp[q];
+            lay[u] = b.lay_s[q];
+        }
+        Window w[U];
+        int64_t row0[U];
+        int a[U][DT_ROWS], e[U][DT_ROWS];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            w[u] = window_of(me[u].x, me[u].y, dr, ev);
+            row0[u] = ev.cell_off + (int64_t)lay[u] * nbxy + (int64_t)w[u].ly * ev.nbx;
+#pragma unroll
+            for (int r = 0; r < DT_ROWS; ++r) {
+                const bool in = w[u].ly + r <= w[u].hy;
+                const int64_t row = row0[u] + (in ? (int64_t)r * ev.nbx : 0);
+                a[u][r] = in ? b.cell_start[row + w[u].lx] : 0;
+                e[u][r] = in ? b.cell_start[row + w[u].hx + 1] : 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * blockDim.x;
+            if (k >= tl.len) continue;
+            const int nr = w[u].hy - w[u].ly + 1;
+            unsigned T = 0;
+            int last = e[u][0];
+#pragma unroll
+            for (int r = 0; r < DT_ROWS; ++r) T += (unsigned)(e[u][r] - a[u][r]);
+            for (int r = DT_ROWS; r < nr; ++r) {  // rows the sorted form does not take
+                const int64_t row = row0[u] + (int64_t)r * ev.nbx;
+                const int u0 = b.cell_start[row + w[u].lx];
+                last = b.cell_start[row + w[u].hx + 1];
+                T += (unsigned)(last - u0);
+            }
+            if (nr > 1 && nr <= DT_ROWS) last = nr == 2 ? e[u][1] : e[u][2];
+            lo = min(lo, a[u][0] - tl.start);
+            hi = max(hi, last - tl.start);
+            rows = max(rows, nr);
+            tsum += T;
+            sh.win[k] = make_uint4(pack_row(a[u][0] - tl.start, e[u][0] - a[u][0]),
+                                   pack_row(a[u][1] - tl.start, e[u][1] - a[u][1]),
+                                   pack_row(a[u][2] - tl.start, e[u][2] - a[u][2]),
+                                   min(T, 65535u));
+            atomicAdd(&sh.hist[DT_BUCKETS - 1 - min((int)T, DT_BUCKETS - 1)], 1);
+        }
+    }
+    lo = __reduce_min_sync(FULL_MASK, lo);
+    hi = __reduce_max_sync(FULL_MASK, hi);
+    rows = __reduce_max_sync(FULL_MASK, rows);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(FULL_MASK, tsum, o);
+    if (lane_id() == 0) {
+        atomicMin(&sh.lo, lo);
+        atomicMax(&sh.hi, hi);
+        atomicMax(&sh.rows, rows);
+        atomicAdd(&sh.tsum, tsum);
+    }
+    __syncthreads();
+}
+
+// Whether the sorted form takes the tile (uniform over the CTA).
+__device__ __forceinline__ bool tile_sorted(const DensityShared &sh) {
+    return sh.rows <= DT_ROWS && sh.lo >= -DT_OUT + 1 && sh.hi <= DT_OUT - 1 &&
+           sh.hi - sh.lo <= BAND_CAP;
+}
+
+// Counting sort of the tile's hits by descending window population (the
+// histogram from tile_windows); order inside a class is arbitrary.
+__device__ __forceinline__ void tile_sort(const Tile &tl, DensityShared &sh) {
+    static_assert(DT_BUCKETS == 64, "one warp scans two classes per lane");
+    if (threadIdx.x < 32) {
+        const int v0 = sh.hist[2 * threadIdx.x], v1 = sh.hist[2 * threadIdx.x + 1];
+        const int incl = warp_incl_scan(v0 + v1);
+        sh.hist[2 * threadIdx.x] = incl - v0 - v1;
+        sh.hist[2 * threadIdx.x + 1] = incl - v1;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+        const int T = (int)sh.win[k].w;
+        const int pos = atomicAdd(&sh.hist[DT_BUCKETS - 1 - min(T, DT_BUCKETS - 1)], 1);
+        sh.perm[pos] = (unsigned short)k;
+    }
+}
+
+// One hit's window as a flat run of T candidates in the staged band: the
+// c-th candidate is at c + base(c), base a step function of c with breaks at
+// the row ends (ROWS = 2: windows of at most two rows, the usual case).
+template <int ROWS>
+struct FlatWin {
+    int b0, b1, b2;  // band index minus c, per row
+    int o1, o2;      // where rows 1 and 2 begin in c
+    int T;
+    __device__ __forceinline__ FlatWin(const uint4 &w, int lo) {
+        const int l0 = row_len(w.x), l1 = row_len(w.y);
+        o1 = l0;
+        o2 = l0 + l1;
+        T = (int)w.w;
+        b0 = row_start(w.x) - lo;
+        b1 = row_start(w.y) - lo - o1;
+        b2 = row_start(w.z) - lo - o2;
+    }
+    __device__ __forceinline__ int at(int c) const {
+        if (ROWS <= 2) return c + (c < o1 ? b0 : b1);
+        return c + (c < o1 ? b0 : (c < o2 ? b1 : b2));
+    }
+};
+
+// ---- rho ---------------------------------------------------------------------
+
+// Sum of a 64-bit integer over the warp (exact).
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// rho of the tile's hits in the sorted form (the band staged, hits ordered).
+template <int CHI, int ROWS>
+__device__ __forceinline__ void rho_sorted(const Buffers &b, const Params &p, const Tile &tl,
+                                           const EventDesc &ev, const FixedW &fw,
+                                           const DensityShared &sh, const float4 *band) {
+    const bool fixed = CHI == 0 && fw.on;
+    const int lo = sh.lo;
+    for (int j = threadIdx.x; j < tl.len; j += blockDim.x) {
+        const int k = sh.perm[j];
+        const int q = tl.start + k;
+        const float4 me = band[k - lo];
+        const FlatWin<ROWS> f(sh.win[k], lo);
+        float r;
+        bool ok;
+        if (fixed) {
+            long long acc = 0;
+#pragma unroll 2
+            for (int c = 0; c < f.T; ++c) {  // branch-free body
+                const float4 h = band[f.at(c)];
+                const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                acc += d2 < p.dc2 ? fixed_weight_of(h) : 0ll;
+            }
+            r = __fmul_rn(__ll2float_rn(acc), fw.unit);
+            ok = 32 - __clz(f.T) <= fw.budget;
+        } else {
+            TwoSumAcc a;
+            for (int c = 0; c < f.T; ++c) {  // branch-free body
+                const float4 h = band[f.at(c)];
+                const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                const bool near = d2 < p.dc2;
+                a.add(near ? term_of<CHI>(d2, h.z, p.chi_inv) : 0.0f, near);
+            }
+            r = __fadd_rn(a.s, a.c);
+            ok = a.exact();
+        }
+        if (!ok) {  // the integer accumulator over the window in global memory
+            const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
+            const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * ev.nbx * ev.nby;
+            r = rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv,
+                              fixed ? fw.unit : 0.0f);
+        }
+        b.rho[q] = r;
+    }
+}
+
+template <int CHI, int U>
+__device__ __forceinline__ void rho_tile(const Buffers &b, const Params &p, int t,
+                                         DensityShared &sh, float4 *band) {
+    const Tile tl = b.tiles[t];
+    const EventDesc ev = b.events[tl.event];
+    const FixedW fw = fixed_weights(b.wexp + 2 * tl.event, CHI);  // uniform per event
+    const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
+    tile_windows<U>(b, tl, ev, p.rwin_rho, sh);
+    const bool fixed = CHI == 0 && fw.on;
+    if (fixed && sh.tsum >= (unsigned long long)DENSE_MEAN * tl.len) {
+        // warp form: lanes stride over one hit's window
+        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int k = warp; k < tl.len; k += nwarps) {
+            const int q = tl.start + k;
+            const float4 me = b.sp[q];
+            const int lay = b.lay_s[q];
+            const int64_t plane = ev.cell_off + (int64_t)lay * nbxy;
+            const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
+            long long acc = 0;
+            unsigned T = 0;
+            for (int by = w.ly; by <= w.hy; ++by) {
+                const int64_t row = plane + (int64_t)by * ev.nbx;
+                const int u0 = b.cell_start[row + w.lx], e = b.cell_start[row + w.hx + 1];
+                T += (unsigned)(e - u0);
+                for (int u = u0 + lane_id(); u < e; u += 32) {
+                    const float4 h = b.sp[u];
+                    const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                    acc += d2 < p.dc2 ? fixed_weight_of(h) : 0ll;
+                }
+            }
+            acc = warp_sum_ll(acc);
+            if (lane_id() == 0)
+                b.rho[q] = 32 - __clz(T) <= fw.budget
+                               ? __fmul_rn(__ll2float_rn(acc), fw.unit)
+                               : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2,
+                                               p.chi_inv, fw.unit);
+        }
+        __syncthreads();  // the shared state is reused by the next tile
+        return;
+    }
+    if (!tile_sorted(sh)) {  // per-hit form
+        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+            const int q = tl.start + k;
+            b.rho[q] = rho_of_hit<CHI>(b, p, ev, fw, b.sp[q], b.lay_s[q]);
+        }
+        __syncthreads();
+        return;
+    }
+    tile_sort(tl, sh);
+    const int lo = sh.lo, n_band = sh.hi - sh.lo;
+    for (int h = threadIdx.x; h < n_band; h += blockDim.x) band[h] = b.sp[tl.start + lo + h];
+    __syncthreads();
+    if (sh.rows <= 2)
+        rho_sorted<CHI, 2>(b, p, tl, ev, fw, sh, band);
+    else
+        rho_sorted<CHI, DT_ROWS>(b, p, tl, ev, fw, sh, band);
+    __syncthreads();
+}
+
+// ---- nh, delta and the decision ----------------------------------------------
+
+// Lexicographic minimum of the 64-bit key over the warp.
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(FULL_MASK, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+// nh of the tile's hits in the sorted form (the band staged as x, y, rho, id).
+template <int ROWS>
+__device__ __forceinline__ void nh_sorted(const Buffers &b, const Params &p, const Tile &tl,
+                                          const DensityShared &sh, const float4 *band) {
+    const int lo = sh.lo;
+    for (int j = threadIdx.x; j < tl.len; j += blockDim.x) {
+        const int k = sh.perm[j];
+        const float4 me = band[k - lo];  // x, y, rho, id
+        const FlatWin<ROWS> f(sh.win[k], lo);
+        unsigned long long best = nh_none(p);
+#pragma unroll 2
+        for (int c = 0; c < f.T; ++c) {  // branch-free body
+            const float4 h = band[f.at(c)];
+            const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+            const unsigned long long key = nh_key(d2, id_of(h));
+            best = (h.z > me.z && key < best) ? key : best;
+        }
+        nh_store(b, p, tl.start + k, id_of(me), me.z, best);
+    }
+}
+
+template <int U>
+__device__ __forceinline__ void nh_tile(const Buffers &b, const Params &p, int t,
+                                        DensityShared &sh, float4 *band) {
+    const Tile tl = b.tiles[t];
+    const EventDesc ev = b.events[tl.event];
+    const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
+    tile_windows<U>(b, tl, ev, p.rwin_nh, sh);
+    if (sh.tsum >= (unsigned long long)DENSE_MEAN * tl.len) {
+        // warp form: lanes stride over one hit's window
+        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int k = warp; k < tl.len; k += nwarps) {
+            const int q = tl.start + k;
+            const float4 me = b.sp[q];
+            const float ri = b.rho[q];
+            const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
+            const Window w = window_of(me.x, me.y, p.rwin_nh, ev);
+            unsigned long long best = nh_none(p);
+            for (int by = w.ly; by <= w.hy; ++by) {
+                const int64_t row = plane + (int64_t)by * ev.nbx;
+                const int e = b.cell_start[row + w.hx + 1];
+                for (int u = b.cell_start[row + w.lx] + lane_id(); u < e; u += 32) {
+                    const float4 h = b.sp[u];
+                    const float d2 = sq_dist(me.x, me.y, h.x, h.y);
+                    const unsigned long long key = nh_key(d2, b.sid[u]);
+                    best = (b.rho[u] > ri && key < best) ? key : best;
+                }
+            }
+            best = warp_min_u64(best);
+            if (lane_id() == 0) nh_store(b, p, q, b.sid[q], ri, best);
+        }
+        __syncthreads();
+        return;
+    }
+    if (!tile_sorted(sh)) {  // per-hit form
+        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+            const int q = tl.start + k;
+            const float4 me = b.sp[q];
+            const float ri = b.rho[q];
+            nh_store(b, p, q, b.sid[q], ri, nh_of_hit(b, p, ev, me.x, me.y, ri, b.lay_s[q]));
+        }
+        __syncthreads();
+        return;
+    }
+    tile_sort(tl, sh);
+    const int lo = sh.lo, n_band = sh.hi - sh.lo;
+    for (int h = threadIdx.x; h < n_band; h += blockDim.x) {
+        const int u = tl.start + lo + h;
+        const float4 r = b.sp[u];
+        band[h] = make_float4(r.x, r.y, b.rho[u], __int_as_float(b.sid[u]));
+    }
+    __syncthreads();
+    if (sh.rows <= 2)
+        nh_sorted<2>(b, p, tl, sh, band);
+    else
+        nh_sorted<DT_ROWS>(b, p, tl, sh, band);
+    __syncthreads();
+}
+
+}  // namespace clue

@@ -23,12 +23,13 @@ cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, c
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256, 2) k_assign(Buffers b) { assign_stage(b); }
+__global__ void __launch_bounds__(256, 2) k_assign(Buffers b, Params p) { assign_stage(b, p); }
 
 // One CTA per tile (chain lengths vary; see launch_rho).
-cudaError_t launch_assign(const Buffers &b, const LaunchCfg &, cudaStream_t s) {
+cudaError_t launch_assign(const Buffers &b, const Params &p, const LaunchCfg &,
+                          cudaStream_t s) {
     const int grid = b.ntiles;
-    k_assign<<<grid > 0 ? grid : 1, 256, 0, s>>>(b);
+    k_assign<<<grid > 0 ? grid : 1, 256, 0, s>>>(b, p);
     return cudaGetLastError();
 }
 
@@ -114,41 +115,56 @@ cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s) 
 
 // Pending followers left after the expansion are noise (their chain ends at an
 // outlier or at a hit with no nearest-higher) unless the expansion stopped
-// with a non-empty frontier (a tree deeper than EXPAND_LEVELS); then
-// each pending hit follows its nh chain to the first hit with a final id (a
-// seed, an expanded follower, or noise).  The chain is finite because rho
-// rises strictly along it; the walk is still bounded by N steps.
-__global__ void __launch_bounds__(256) k_complete(Buffers b) {
+// with a non-empty frontier (a tree deeper than EXPAND_LEVELS); then each
+// pending hit follows its nh chain, at most min(CHASE_STEPS, walk limit)
+// steps, to the first hit with a final id (a seed, an expanded follower, or
+// noise); hits of longer chains are finished by pointer jumping (k_jump).
+// Ids other threads finalise meanwhile only shorten a walk.
+__global__ void __launch_bounds__(256) k_complete(Buffers b, Params p) {
     const bool ovf = b.ctrl->overflow != 0 || b.ctrl->fsize[EXPAND_LEVELS % 3] != 0;
+    const int kmax = min(CHASE_STEPS, p.walk_limit);
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];
-        for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+        for (int k0 = 0; k0 < tl.len; k0 += blockDim.x) {
+            const int k = k0 + threadIdx.x;
             const int g = tl.start + k;
-            if (b.cid[g] != PENDING) continue;
-            if (!ovf) {
-                b.cid[g] = -1;
-                continue;
+            bool pend = false;
+            int v = 0;
+            if (k < tl.len && b.cid[g] == PENDING) {
+                if (!ovf) {
+                    b.cid[g] = -1;
+                } else {
+                    v = b.code[g];
+                    int cv = __ldcg(&b.cid[v]);
+                    for (int steps = 1; cv == PENDING && steps < kmax; ++steps) {
+                        v = b.code[v];
+                        cv = __ldcg(&b.cid[v]);
+                    }
+                    if (cv != PENDING) b.cid[g] = cv;
+                    pend = cv == PENDING;  // v: an unresolved ancestor
+                }
             }
-            int v = b.code[g];
-            int cv = b.cid[v];
-            int64_t steps = 0;
-            while (cv == PENDING && steps < b.N) {
-                v = b.code[v];
-                cv = b.cid[v];
-                ++steps;
-            }
-            if (cv == PENDING) {
-                atomicOr(&b.ctrl->err, ERRBIT_TIMEOUT);
-                cv = -1;
-            }
-            b.cid[g] = cv;
+            pend_hit(b, FULL_MASK, pend, g, v);  // the k0 loop is uniform over the CTA
         }
     }
 }
 
-cudaError_t launch_complete(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
+cudaError_t launch_complete(const Buffers &b, const Params &p, const LaunchCfg &c,
+                            cudaStream_t s) {
     const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
-    k_complete<<<grid > 0 ? grid : 1, c.block_fill, 0, s>>>(b);
+    k_complete<<<grid > 0 ? grid : 1, c.block_fill, 0, s>>>(b, p);
+    return cudaGetLastError();
+}
+
+// The pointer jumping of the hits a bounded walk left pending, by one CTA
+// (it returns at once when there are none, the usual case).
+__global__ void __launch_bounds__(1024) k_jump(Buffers b, Params p) {
+    const int np = b.ctrl->npend;
+    if (np > 0) jump_rounds(b, np, p.walk_limit - min(CHASE_STEPS, p.walk_limit));
+}
+
+cudaError_t launch_jump(const Buffers &b, const Params &p, cudaStream_t s) {
+    k_jump<<<1, 1024, 0, s>>>(b, p);
     return cudaGetLastError();
 }
 
@@ -160,9 +176,9 @@ __global__ void __launch_bounds__(256) k_export(Buffers b, float *rho, float *de
         const int64_t hoff = b.events[tl.event].hit_off;
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
-            const int g = __float_as_int(b.spr[q].w);
+            const int g = b.sid[q];
             const float2 h = b.hr[q];
-            if (rho) rho[g] = b.spr[q].z;
+            if (rho) rho[g] = b.rho[q];
             if (delta) delta[g] = sqrtf(h.x);
             if (nh) {
                 const int j = __float_as_int(h.y);

@@ -1,14 +1,24 @@
-// Steps S2 and S3 as per-stage kernels; the stage bodies and their
-// description are in density_stages.cuh.
-#include "density_stages.cuh"
+// Steps S2 and S3 as per-stage kernels, one CTA per tile; the tile bodies and
+// their description are in density_tile.cuh.
+#include "density_tile.cuh"
 
 namespace clue {
 
 // Each density kernel in two builds: CTAs of up to 256 threads (the usual
-// case; the compiler's register choice then keeps several CTAs per SM) and of
-// up to 1024 (runs with fewer tiles than SMs: one hit per thread).
+// case: four per SM, each with ~46 KB of shared memory) and of up to 1024
+// (runs with fewer tiles than SMs: one hit per thread).
+// The window pass of a thread issues the loads of DT_ILP hits together.
+constexpr int DT_ILP = 2;
+
+// The 256-thread build keeps to 64 registers, so that four CTAs share an SM
+// (their shared memory allows four).
 template <int CHI, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_rho(Buffers b, Params p) { rho_stage<CHI>(b, p); }
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 1) k_rho(Buffers b, Params p) {
+    __shared__ DensityShared sh;
+    __shared__ float4 band[BAND_CAP];
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x)
+        rho_tile<CHI, DT_ILP>(b, p, t, sh, band);
+}
 
 template <int CHI>
 void launch_rho_k(int grid, int block, cudaStream_t s, const Buffers &b, const Params &p) {
@@ -18,8 +28,8 @@ void launch_rho_k(int grid, int block, cudaStream_t s, const Buffers &b, const P
         k_rho<CHI, 256><<<grid, block, 0, s>>>(b, p);
 }
 
-// One CTA per tile: hits differ widely in window population, and the
-// hardware's CTA scheduling balances that better than a persistent grid.
+// One CTA per tile: tiles differ widely in work, and the hardware's CTA
+// scheduling balances that better than a persistent grid.
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
     const int grid = b.ntiles;
     const int g = grid > 0 ? grid : 1;
@@ -33,7 +43,12 @@ cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cu
 }
 
 template <int MAXT>
-__global__ void __launch_bounds__(MAXT) k_nh(Buffers b, Params p) { nh_stage(b, p); }
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 1) k_nh(Buffers b, Params p) {
+    __shared__ DensityShared sh;
+    __shared__ float4 band[BAND_CAP];
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x)
+        nh_tile<DT_ILP>(b, p, t, sh, band);
+}
 
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
     const int grid = b.ntiles;

@@ -556,6 +556,73 @@ def test_long_chain(clue_mod):
     assert_parity(_gpu_all(cl, ev, p), ref)
 
 
+def _chain_1000():
+    n = 1000
+    x = np.arange(n, dtype=np.float64)
+    w = 1.0 + np.arange(n) * 1e-3
+    ev = Ev(x - 500.0, np.zeros(n), np.zeros(n, np.int32), w)
+    return ev, (1.5, 1.0, 2.0, 3.0), (-600.0, 600.0, -10.0, 10.0)
+
+
+@pytest.mark.parametrize("expand", [0, 1], ids=["frontier", "chase"])
+def test_walk_limit_runs_out_and_reports_timeout(clue_mod, expand):
+    """The 1000-hit chain (one cluster, depth 999) under walk limits too short
+    for it: 10 steps (the bounded walk alone) and 66 (the 64-step walk and two
+    pointer-jumping rounds).  The device gives up on the hits it cannot reach
+    (-1), the next clue_sync returns CLUE_ERR_TIMEOUT, and the context stays
+    usable.  With 74 (ten rounds) the chain resolves exactly."""
+    ev, p, ext = _chain_1000()
+    ref = oracle.run_event(ev, p, 1, extent=ext)
+    assert ref["n_seeds"] == 1 and (ref["cluster_id"] == 0).all()
+    for limit in (10, 66):
+        cl = _cl(clue_mod, ext, 1, expand=expand, walk_limit=limit)
+        cid, seed = cl.run(ev.x, ev.y, ev.layer, ev.energy, p)
+        with pytest.raises(clue_mod.ClueError) as ei:
+            cl.sync()
+        assert ei.value.code == clue_mod.CLUE_ERR_TIMEOUT
+        c = cid.cpu().numpy()
+        assert set(np.unique(c).tolist()) == {-1, 0}
+        assert c[-1] == 0 and c[0] == -1  # the seed is resolved, the chain's far end is not
+        assert np.array_equal(seed.cpu().numpy(), ref["is_seed"])
+        small = gen.make_event(3000, 1, 5, "blobs", extent=ext)
+        g = _gpu_all(cl, small, gen.PARAMS_BLOBS)  # syncs: no error left behind
+        assert_parity(g, oracle.run_event(small, gen.PARAMS_BLOBS, 1, extent=ext))
+        cl.close()
+    cl = _cl(clue_mod, ext, 1, expand=expand, walk_limit=74)
+    assert_parity(_gpu_all(cl, ev, p), ref)
+
+
+def _serpentine_chain(n, row_len=1300):
+    """n hits on a serpentine path, 1.5 cm apart along rows 3 cm apart, with
+    weights rising along the path (exact in fp32): every hit's nearest-higher
+    is the next hit or, at a row's end, one of the next row's first two, so
+    the event is one cluster whose tree is a single chain of depth ~n."""
+    i = np.arange(n)
+    r, c = i // row_len, i % row_len
+    c = np.where(r % 2 == 0, c, row_len - 1 - c)
+    x = c * 1.5 - row_len * 0.75
+    y = r * 3.0 - 240.0
+    w = 1.0 + i * 2.0 ** -20
+    return Ev(x, y, np.zeros(n, np.int32), w)
+
+
+@pytest.mark.parametrize("expand", [0, 1], ids=["frontier", "chase"])
+def test_chain_of_200k_hits(clue_mod, expand):
+    """A 200k-hit chain, resolved by the bounded walk plus pointer jumping in
+    about log2(200k / 64) rounds, against the oracle in full."""
+    ev = _serpentine_chain(200_000)
+    p = (2.0, 1.0, 3.5, 4.0)
+    ext = (-1000.0, 1000.0, -250.0, 250.0)
+    ref = oracle.run_event(ev, p, 1, extent=ext)
+    assert ref["n_seeds"] == 1 and (ref["cluster_id"] == 0).all()
+    depth, j = 0, 0  # the chain really is deep: follow nh from the first hit
+    while j >= 0 and depth <= ev.n:
+        j, depth = int(ref["nh"][j]), depth + 1
+    assert depth > 190_000
+    cl = _cl(clue_mod, ext, 1, expand=expand)
+    assert_parity(_gpu_all(cl, ev, p), ref)
+
+
 def test_invalid_inputs_reported_at_sync(clue_mod):
     cl = _cl(clue_mod, gen.EXTENT, 4)
     x = np.zeros(100, np.float32)
@@ -591,7 +658,7 @@ def test_autotune_keeps_results(clue_mod):
 
 def test_stage_times_and_launch_count(clue_mod):
     ev = gen.make_event(100_000, 100, 3, "blobs")
-    for expand, last in ((0, {"expand_level", "complete"}), (1, {"assign"})):
+    for expand, last in ((0, {"expand_level", "complete", "jump"}), (1, {"assign", "jump"})):
         cl = _cl(clue_mod, gen.EXTENT, 100, expand=expand)
         cl.set_profiling(True)
         cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_BLOBS)
@@ -600,8 +667,9 @@ def test_stage_times_and_launch_count(clue_mod):
         assert all(v >= 0 for v in st.values())
         kt = cl.kernel_times()
         assert {"fill_cells", "rho", "nh_delta"} | last <= set(kt)
-        # two-level grid fill with a one-CTA segment scan (4); chase: one-CTA seed-rank scan
-        assert cl.launch_count() == (4 + 19 if expand == 0 else 8)
+        # two-level grid fill with a one-CTA segment scan (4); chase: one-CTA
+        # seed-rank scan; both end with the pointer-jumping kernel
+        assert cl.launch_count() == (4 + 20 if expand == 0 else 9)
 
 
 def test_paper_parameter_workload(clue_mod):
