@@ -227,7 +227,8 @@ def parse_traffic():
 
 
 # Host-side sources: a change there leaves the kernels' traffic unchanged.
-HOST_SOURCES = {"clue_api.cu", "clue_static.cu"}
+HOST_SOURCES = {"clue_api.cu", "clue_static.cu", "clue_serve.cu", "serve_core.cpp",
+                "serve_core.h"}
 
 
 def source_hash():
@@ -303,6 +304,10 @@ def extra_configs(torch, clue, tuning, dev, args):
 
 
 def served(torch, clue, tuning, dev, peak_mhits, args):
+    """The served stream: Poisson arrivals of events from a pool (log-uniform
+    10k-2M hits, pinned host memory) through the library's server at offered
+    loads of `args.loads` x the batched rate; latency from submission to the
+    results in host memory."""
     from paper_2001_09761_gb300 import serve
     rng_sizes = gen.batch_sizes(args.pool, 1e4, 2e6, seed=7)
     pool = []
@@ -311,22 +316,22 @@ def served(torch, clue, tuning, dev, peak_mhits, args):
         pin = lambda a: torch.from_numpy(a).pin_memory()
         pool.append((pin(ev.x), pin(ev.y), pin(ev.layer), pin(ev.energy)))
     mean_hits = float(np.mean(rng_sizes))
-    out = {"pool_events": len(pool), "mean_hits": mean_hits, "loads": {}}
+    out = {"pool_events": len(pool), "mean_hits": mean_hits, "requests": args.requests,
+           "latency": "submit to results in host memory", "loads": {}}
     for load in args.loads:
-        be = serve.GpuBackend(device=dev.index, extent=gen.EXTENT, max_layers=100,
-                              params=PARAMS, region_hits=16_000_000, n_regions=3, tuning=tuning)
         free, _ = torch.cuda.mem_get_info(dev)
-        srv = serve.Server(be, mem_budget_bytes=int(0.5 * free))
+        srv = serve.Server(device=dev.index, extent=gen.EXTENT, max_layers=100, params=PARAMS,
+                           region_hits=16_000_000, n_regions=3, tuning=tuning,
+                           mem_budget_bytes=int(0.5 * free))
+        serve.offered_load(srv, pool[:4], rate_events_per_s=1e3, n_requests=8, seed=1)  # warm
+        srv.reset_stats()
         rate = load * peak_mhits * 1e6 / mean_hits
-        serve.offered_load(srv, pool[:2], rate_events_per_s=1e3, n_requests=4, seed=1)  # warm
-        srv2 = srv
-        srv2.lat, srv2.done_hits, srv2.t_first, srv2.t_last = [], 0, None, None
-        srv2.batches, srv2.batch_sizes = 0, []
-        serve.offered_load(srv2, pool, rate_events_per_s=rate, n_requests=args.requests,
+        serve.offered_load(srv, pool, rate_events_per_s=rate, n_requests=args.requests,
                            seed=int(load * 100))
-        st = srv2.stats()
-        srv2.close()
+        st = srv.stats()
+        srv.close()
         st["offered_events_per_s"] = rate
+        st["offered_mhits_per_s"] = rate * mean_hits / 1e6
         out["loads"][str(load)] = st
     return out
 

@@ -109,19 +109,25 @@ typedef struct clue_opts {
 #define CLUE_EXPAND_CHASE 1
 
 /* Defaults: device 0, extent [-250, 250]^2, 128 layers, tuned bin/block,
- * graphs on, own stream, expansion by chasing (CLUE_EXPAND_CHASE). */
+ * graphs on, own stream, expansion by chasing (CLUE_EXPAND_CHASE), flat chi
+ * (Eq. 3, Algorithm 1), no scratch or walk limit. */
 void clue_default_opts(clue_opts *opts);
 
-/* Create a context on opts->device.  *out receives the context.
+/* Create a context on opts->device.  *out receives the context.  The
+ * context holds what Sec. 4.2 allocates once before the event loop (the
+ * device scratch every run reuses, grown only when a larger run needs it) and
+ * the fixed grid's extent and layer count (Sec. 2.1).
  * Errors: CLUE_ERR_ARG (null, extent not finite/increasing, max_layers < 1,
  * bin_size < 0, block_size, expand or chi out of range, chi_param not > 0
- * for a non-flat chi), CLUE_ERR_CUDA. */
+ * for a non-flat chi, walk_limit < 0), CLUE_ERR_CUDA. */
 int clue_create(clue_ctx **out, const clue_opts *opts);
 
-/* Release the context and everything it owns (waits for its work first). */
+/* Release the context and everything it owns, after waiting for its queued
+ * work: the one-time release after the last event of Sec. 4.2. */
 void clue_destroy(clue_ctx *ctx);
 
-/* Queue later work on another stream (cudaStream_t; NULL = the context's own). */
+/* Queue later work on another stream (cudaStream_t; NULL = the context's own).
+ * The paper has no counterpart: stream placement is a deployment concern. */
 int clue_set_stream(clue_ctx *ctx, void *stream);
 
 /*
@@ -146,7 +152,10 @@ int clue_run(clue_ctx *ctx, const float *x, const float *y, const int32_t *layer
 
 /*
  * Cluster a batch of independent events in one pass (one launch per stage for
- * the whole batch).  Event e owns hits [offsets[e], offsets[e+1]) of the
+ * the whole batch): Sec. 3's pipeline of one kernel per CLUE step over one
+ * structure of arrays, with many events' hits in that structure instead of
+ * one event's; each event is clustered exactly as clue_run clusters it
+ * alone (Algorithms 1-3).  Event e owns hits [offsets[e], offsets[e+1]) of the
  * concatenated device arrays x, y, layer, energy, cluster_id, is_seed.
  *   offsets   HOST int64[n_events + 1], offsets[0] = 0, non-decreasing,
  *             offsets[n_events] <= 2^31 - 2
@@ -161,7 +170,9 @@ int clue_run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t 
 
 /*
  * As clue_run_batch, but every array (x, y, layer, energy, cluster_id,
- * is_seed, offsets) is a HOST pointer (pinned memory is fastest).  The call
+ * is_seed, offsets) is a HOST pointer (pinned memory is fastest): the
+ * end-to-end path whose host-device copies Table 2 of Sec. 4.2 lists as
+ * "cuda memcpy".  The call
  * copies the inputs to context-owned device buffers, clusters, copies the
  * results back and returns when they are in host memory (it synchronises).
  * A batch of 8M hits or more is split at event boundaries into chunks of
@@ -175,6 +186,7 @@ int clue_run_batch_host(clue_ctx *ctx, const float *x, const float *y, const int
                         int32_t *cluster_id, uint8_t *is_seed);
 
 /*
+ * (The paper has no counterpart: a staging helper for servers.)
  * Queue the copies of one event's inputs, n hits of the arrays x, y, layer,
  * energy (host or device; pinned host memory gives asynchronous copies, and
  * pageable host memory may be reused once the call returns), into the DEVICE
@@ -187,8 +199,10 @@ int clue_stage_event(const float *x, const float *y, const int32_t *layer,
                      const float *energy, int64_t n, float *dx, float *dy, int32_t *dlayer,
                      float *denergy, int64_t offset, void *stream);
 
-/* Wait for the context's queued work; returns the first deferred error
- * (CLUE_ERR_INPUT, CLUE_ERR_TIMEOUT, CLUE_ERR_CUDA) or CLUE_OK, and clears it. */
+/* Wait for the context's queued work (the kernels of Sec. 3 run
+ * asynchronously; results are complete once they have all finished); returns
+ * the first deferred error (CLUE_ERR_INPUT, CLUE_ERR_TIMEOUT, CLUE_ERR_CUDA)
+ * or CLUE_OK, and clears it. */
 int clue_sync(clue_ctx *ctx);
 
 /*
@@ -201,9 +215,11 @@ int clue_sync(clue_ctx *ctx);
 int clue_get_intermediates(clue_ctx *ctx, float *rho, float *delta, int32_t *nh);
 
 /*
- * Tune the grid bin size per event-size class (each class timed on its own
- * events, copied into a context-owned sub-batch) and the density kernels'
- * block size (timed on the whole batch) for the given device batch (same
+ * Tune the grid bin size (Sec. 2.1 leaves it free; results do not depend on
+ * it) and the tile length (hits per CTA, so hits per thread) per event-size
+ * class (each class timed on its own events, copied into a context-owned
+ * sub-batch), and the density kernels' block size (Sec. 3 times block sizes
+ * 1024 and 256; here timed on the whole batch) for the given device batch (same
  * arguments as clue_run_batch; results of the trial runs are written to
  * cluster_id / is_seed).  Every candidate gives bit-identical results; only
  * speed differs.  `reps` timed repetitions per candidate (>= 1).
@@ -214,16 +230,21 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
                   float rhoc, float delta_c, float delta_o, int32_t *cluster_id,
                   uint8_t *is_seed, int32_t reps);
 
-/* Write the tuning table as text "class_lo class_hi bin_scale block\n..." into
- * buf (capacity cap bytes, NUL-terminated); returns the length needed, or a
- * negative CLUE_ERR_* code. */
+/* Write the tuning table as text into buf (capacity cap bytes,
+ * NUL-terminated): a comment line, then per class "class <lo> <hi>
+ * <bin_scale> <tile_hits>" (bin size = bin_scale * 2 d_c; tile_hits: hits
+ * per CTA of the per-tile kernels, a multiple of 32 up to 1024), then
+ * "block <threads>" (0 = by run size).  Returns the length needed, or a
+ * negative CLUE_ERR_* code.  (No counterpart in the paper: tuning state.) */
 int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap);
 
-/* Replace the tuning table from text in the format of clue_get_tuning.
- * Errors: CLUE_ERR_ARG on malformed text. */
+/* Replace the tuning table from text in the format of clue_get_tuning (a
+ * class line without <tile_hits> keeps 1024).  Errors: CLUE_ERR_ARG on
+ * malformed text or values out of range. */
 int clue_set_tuning(clue_ctx *ctx, const char *text);
 
-/* Per-kernel timing: when on (1), the next runs record a CUDA event before
+/* (No counterpart in the paper beyond the per-kernel times of Table 2.)
+ * Per-kernel timing: when on (1), the next runs record a CUDA event before
  * the first kernel and after each kernel (or launch group: a prefix sum's
  * three kernels count as one).  clue_stage_times waits for the last profiled
  * run and writes up to `cap` durations in ms, in launch order, and their
@@ -238,10 +259,12 @@ int clue_stage_times(clue_ctx *ctx, float *ms, int32_t cap, char *names, int64_t
 int clue_stage_times_back(clue_ctx *ctx, int32_t back, float *ms, int32_t cap, char *names,
                           int64_t names_cap);
 
-/* Number of kernels the last run launched (for launch accounting). */
+/* Number of kernels the last run launched (for launch accounting; no
+ * counterpart in the paper). */
 int32_t clue_last_launch_count(clue_ctx *ctx);
 
-/* Device bytes the context's scratch arena holds now. */
+/* Device bytes the context's scratch arena holds now (the one-time
+ * allocation of Sec. 4.2). */
 int64_t clue_scratch_bytes(clue_ctx *ctx);
 
 /*
@@ -288,13 +311,89 @@ int clue_run_static(const float *x, const float *y, const int32_t *layer, const 
                     float x_max, float y_min, float y_max, int32_t max_layers,
                     int32_t *cluster_id, uint8_t *is_seed, void *stream);
 
-/* Human-readable text of a CLUE_ERR_* code. */
+/*
+ * Continuous-batching server (the paper has no counterpart: its events are
+ * clustered one at a time; this serves a stream of them on one GPU).
+ *
+ * Events arrive one per clue_server_submit, from any host thread, at any
+ * time.  A worker thread admits each into the device region being filled
+ * while the region has room (hits, events) and the memory budget covers it
+ * (otherwise the event waits), copies its inputs there on a copy stream at
+ * once, and launches a filled region as one clue_run_batch as soon as fewer
+ * than max_inflight batches are queued on the device; the results are copied
+ * back into the event's own output arrays and a stream callback then marks
+ * the event done.  Each event's results are the same bytes as clue_run gives
+ * for the event alone.
+ */
+typedef struct clue_server clue_server;
+
+typedef struct clue_server_opts {
+    int64_t region_hits;          /* hits per device region: the largest event taken */
+    int32_t n_regions;            /* regions, >= 2: one fills while others run */
+    int32_t max_inflight;         /* batches queued on the device at once (<= n_regions - 1) */
+    int32_t max_events_per_batch; /* events per batch at most */
+    int64_t mem_budget_bytes;     /* 0 = none; else each admitted hit holds 141 bytes
+                                     against it until its event is done */
+} clue_server_opts;
+
+/* Defaults: regions of 16M hits, 3 regions, 2 batches in flight, 512 events
+ * per batch, no budget. */
+void clue_server_default_opts(clue_server_opts *opts);
+
+/* Create a server on opts->device with its own context (clue_opts as for
+ * clue_create; opts->stream is ignored: the server owns its streams), the
+ * clustering parameters of every event (as clue_run) and an optional tuning
+ * table (text of clue_get_tuning, or NULL).  Allocates its regions
+ * (n_regions x region_hits x 21 bytes) and starts its worker thread.
+ * Errors: CLUE_ERR_ARG, CLUE_ERR_OOM, CLUE_ERR_CUDA. */
+int clue_server_create(clue_server **out, const clue_opts *opts,
+                       const clue_server_opts *server_opts, float dc, float rhoc,
+                       float delta_c, float delta_o, const char *tuning);
+
+/* Queue one event of n hits.  x, y, layer, energy (inputs) and cluster_id,
+ * is_seed (outputs) are HOST arrays of n entries (pinned memory gives
+ * asynchronous copies); the caller keeps all six valid until the event's
+ * clue_server_wait returns.  *ticket identifies the event.  Errors:
+ * CLUE_ERR_ARG (null pointers, n < 0, n above region_hits or the budget:
+ * nothing queued), CLUE_ERR_STATE (the server is stopping). */
+int clue_server_submit(clue_server *server, const float *x, const float *y,
+                       const int32_t *layer, const float *energy, int64_t n,
+                       int32_t *cluster_id, uint8_t *is_seed, int64_t *ticket);
+
+/* Wait until the ticket's event is done: its results are in its output
+ * arrays.  timeout_s < 0 waits without limit.  Returns CLUE_OK once it is
+ * done, with the event's outcome in *status (CLUE_OK, or CLUE_ERR_INPUT /
+ * CLUE_ERR_TIMEOUT raised on the device by its batch, or CLUE_ERR_CUDA) and
+ * *latency_ms from submission to the results in host memory (either may be
+ * NULL); the ticket is then released.  Returns CLUE_ERR_TIMEOUT, the ticket
+ * kept, if the event is not done in time; CLUE_ERR_ARG for an unknown or
+ * released ticket. */
+int clue_server_wait(clue_server *server, int64_t ticket, double timeout_s, int32_t *status,
+                     double *latency_ms);
+
+/* Counters into out[6] (if not NULL): events done, hits done, batches
+ * launched, events rejected, seconds from the first submission to the last
+ * completion, mean events per batch; and up to `cap` per-event latencies in
+ * ms (completion order) into latency_ms.  Returns the number of latencies
+ * recorded, or a negative CLUE_ERR_* code. */
+int64_t clue_server_stats(clue_server *server, double *out, double *latency_ms, int64_t cap);
+
+/* Start the counters and latencies of clue_server_stats again from zero
+ * (e.g. after a warm-up).  Errors: CLUE_ERR_ARG. */
+int clue_server_reset_stats(clue_server *server);
+
+/* Finish every queued event, stop the worker and release everything. */
+void clue_server_destroy(clue_server *server);
+
+/* Human-readable text of a CLUE_ERR_* code (the paper has no counterpart:
+ * error reporting of this library). */
 const char *clue_strerror(int code);
 
-/* Text of the last CUDA error the context saw ("" if none). */
+/* Text of the last CUDA error the context saw ("" if none; no counterpart in
+ * the paper). */
 const char *clue_last_message(clue_ctx *ctx);
 
-/* Library version string. */
+/* Library version string (no counterpart in the paper). */
 const char *clue_version(void);
 
 #ifdef __cplusplus

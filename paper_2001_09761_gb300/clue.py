@@ -29,6 +29,8 @@ ABI_SYMBOLS = [
     "clue_autotune", "clue_get_tuning", "clue_set_tuning", "clue_set_profiling",
     "clue_stage_times", "clue_stage_times_back", "clue_last_launch_count", "clue_scratch_bytes", "clue_strerror",
     "clue_last_message", "clue_version", "clue_run_static", "clue_stage_event",
+    "clue_server_default_opts", "clue_server_create", "clue_server_submit", "clue_server_wait",
+    "clue_server_stats", "clue_server_reset_stats", "clue_server_destroy",
 ]
 
 

@@ -43,6 +43,7 @@ int class_of(int64_t n) {
 
 struct GraphEntry {
     uint64_t sig = 0;
+    std::vector<unsigned char> key;  // the fields `sig` hashes, compared on a hash match
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;  // kept while profiled: its event-record nodes
     std::vector<cudaGraphNode_t> evnodes;  // node stamping profiling event k
@@ -147,7 +148,7 @@ int check_params(float dc, float rhoc, float delta_c, float delta_o) {
 }
 
 Params make_params(const clue_ctx *ctx, float dc, float rhoc, float delta_c, float delta_o) {
-    Params p;
+    Params p{};
     const float dm = delta_o > delta_c ? delta_o : delta_c;
     p.dc2 = dc * dc;
     p.dm2 = dm * dm;
@@ -501,18 +502,25 @@ int find_event_nodes(clue_ctx *ctx, GraphEntry &g, int nev) {
     return CLUE_OK;
 }
 
+// What identifies a run's launch sequence: the event table (sizes, grids,
+// offsets), the caller's pointers, the parameters, the launch configuration,
+// profiling and the arena.  Serialised into `key`; returns its hash.
 uint64_t signature(const clue_ctx *ctx, const Plan &plan, const Buffers &b, const Params &p,
-                   const LaunchCfg &cfg) {
-    uint64_t h = 1469598103934665603ULL;
-    h = fnv(h, plan.ev.data(), plan.ev.size() * sizeof(EventDesc));
+                   const LaunchCfg &cfg, std::vector<unsigned char> &key) {
+    key.clear();
+    auto put = [&](const void *d, size_t n) {
+        const unsigned char *c = (const unsigned char *)d;
+        key.insert(key.end(), c, c + n);
+    };
+    put(plan.ev.data(), plan.ev.size() * sizeof(EventDesc));
     const void *ptrs[6] = {b.x, b.y, b.layer, b.w, b.cid, b.is_seed};
-    h = fnv(h, ptrs, sizeof(ptrs));
-    h = fnv(h, &p, sizeof(p));
-    h = fnv(h, &cfg, sizeof(cfg));
+    put(ptrs, sizeof(ptrs));
+    put(&p, sizeof(p));
+    put(&cfg, sizeof(cfg));
     const int prof = ctx->profiling;
-    h = fnv(h, &prof, sizeof(prof));
-    h = fnv(h, &ctx->arena, sizeof(ctx->arena));
-    return h;
+    put(&prof, sizeof(prof));
+    put(&ctx->arena, sizeof(ctx->arena));
+    return fnv(1469598103934665603ULL, key.data(), key.size());
 }
 
 // The shape of a run's launch sequence: expansion mode, form of the grid
@@ -614,9 +622,10 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
 
     const bool graphs = allow_graph && ctx->opts.use_graphs && ctx->stream != nullptr;
     if (graphs) {
-        const uint64_t sig = signature(ctx, plan, b, p, cfg);
+        std::vector<unsigned char> key;
+        const uint64_t sig = signature(ctx, plan, b, p, cfg, key);
         for (auto &g : ctx->graphs)
-            if (g.sig == sig) {
+            if (g.sig == sig && g.key == key) {
                 if (ctx->profiling) {
                     rc = graph_use_set(ctx, g);
                     if (rc) return rc;
@@ -645,6 +654,7 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
             }
             GraphEntry g;
             g.sig = sig;
+            g.key = std::move(key);
             const size_t tb = tables_bytes(plan);
             std::vector<char> host(tb);
             fill_tables(plan, host.data());
@@ -713,6 +723,10 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
 }
 
 }  // namespace
+
+namespace clue {
+unsigned *ctx_error_word(clue_ctx *ctx) { return &ctx->d_ctrl->err; }
+}  // namespace clue
 
 extern "C" {
 

@@ -194,3 +194,11 @@ cudaError_t launch_export(const Buffers &b, const LaunchCfg &c, float *rho, floa
 int64_t scan_partials_needed(int64_t n);
 
 }  // namespace clue
+
+struct clue_ctx;
+namespace clue {
+// The context's sticky device error word (ERRBIT_*), for the server, which
+// reads it back after each batch.
+unsigned *ctx_error_word(clue_ctx *ctx);
+
+}  // namespace clue

@@ -44,6 +44,15 @@ def test_host_only_calls(lib):
         clue.CLUE_ERR_ARG
     assert lib.clue_sync(None) == clue.CLUE_ERR_ARG
     assert lib.clue_create(None, None) == clue.CLUE_ERR_ARG
+    from paper_2001_09761_gb300 import serve
+    serve._lib()
+    so = serve.ClueServerOpts()
+    lib.clue_server_default_opts(so)
+    assert (so.n_regions, so.max_inflight, so.max_events_per_batch) == (3, 2, 512)
+    assert lib.clue_server_create(None, None, None, 2.0, 2.0, 2.0, 4.0, None) == \
+        clue.CLUE_ERR_ARG
+    assert lib.clue_server_submit(None, None, None, None, None, 5, None, None, None) == \
+        clue.CLUE_ERR_ARG
 
 
 def test_library_has_no_oracle_dependency():

@@ -641,6 +641,32 @@ def test_invalid_inputs_reported_at_sync(clue_mod):
     assert ei.value.code == clue_mod.CLUE_ERR_ARG
 
 
+@pytest.mark.parametrize("tile", [64, 256, 512, 1024])
+@pytest.mark.parametrize("block", [0, 128, 512])
+def test_tile_length_and_block_do_not_change_results(clue_mod, tile, block):
+    """Every tuning choice of the table (hits per tile, so hits per thread, per
+    size class; the density kernels' block) gives the same bytes: a batch with
+    an event in each size class, against the oracle."""
+    evs = [gen.make_event(n, 100, 700 + i, "blobs") for i, n in
+           enumerate([12000, 50000, 150000, 400000, 1_100_000])]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = _cl(clue_mod, gen.EXTENT, 100)
+    lines = [ln for ln in cl.tuning.splitlines() if ln.startswith("class")]
+    cl.tuning = "\n".join(" ".join(ln.split()[:4] + [str(tile)]) for ln in lines) + \
+        f"\nblock {block}\n"
+    assert all(ln.split()[4] == str(tile) for ln in cl.tuning.splitlines()
+               if ln.startswith("class"))
+    cid, seed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    rho, delta, nh = cl.intermediates()
+    cl.sync()
+    c, sd = cid.cpu().numpy(), seed.cpu().numpy()
+    r, d, h = rho.cpu().numpy(), delta.cpu().numpy(), nh.cpu().numpy()
+    for i, ev in enumerate(evs):
+        a, z = offs[i], offs[i + 1]
+        g = dict(cluster_id=c[a:z], is_seed=sd[a:z], rho=r[a:z], delta=d[a:z], nh=h[a:z])
+        assert_parity(g, oracle.run_event(ev, gen.PARAMS_BLOBS, 100))
+
+
 def test_autotune_keeps_results(clue_mod):
     evs = [gen.make_event(n, 100, 900 + i, "blobs") for i, n in enumerate([15000, 60000, 200000])]
     x, y, l, e, offs = gen.concat(evs)
@@ -654,6 +680,11 @@ def test_autotune_keeps_results(clue_mod):
         assert np.array_equal(cid[offs[i]:offs[i + 1]],
                               oracle.run_event(ev, gen.PARAMS_BLOBS, 100)["cluster_id"])
     cl.tuning = table  # round-trips through the text format
+    assert cl.tuning == table
+    assert len([ln for ln in table.splitlines() if ln.startswith("class")]) == 5
+    for ln in table.splitlines():
+        if ln.startswith("class"):
+            assert int(ln.split()[4]) in (256, 512, 1024)
 
 
 def test_stage_times_and_launch_count(clue_mod):
