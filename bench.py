@@ -307,7 +307,7 @@ def served(torch, clue, tuning, dev, peak_mhits, args):
     """The served stream: Poisson arrivals of events from a pool (log-uniform
     10k-2M hits, pinned host memory) through the library's server at offered
     loads of `args.loads` x the batched rate; latency from submission to the
-    results in host memory."""
+    results on the device (the inputs' copy from the host included)."""
     from paper_2001_09761_gb300 import serve
     rng_sizes = gen.batch_sizes(args.pool, 1e4, 2e6, seed=7)
     pool = []
@@ -317,7 +317,8 @@ def served(torch, clue, tuning, dev, peak_mhits, args):
         pool.append((pin(ev.x), pin(ev.y), pin(ev.layer), pin(ev.energy)))
     mean_hits = float(np.mean(rng_sizes))
     out = {"pool_events": len(pool), "mean_hits": mean_hits, "requests": args.requests,
-           "latency": "submit to results in host memory", "loads": {}}
+           "latency": "submit to results on the device (host input copy included)",
+           "loads": {}}
     for load in args.loads:
         free, _ = torch.cuda.mem_get_info(dev)
         srv = serve.Server(device=dev.index, extent=gen.EXTENT, max_layers=100, params=PARAMS,

@@ -351,9 +351,10 @@ int clue_server_create(clue_server **out, const clue_opts *opts,
                        float delta_c, float delta_o, const char *tuning);
 
 /* Queue one event of n hits.  x, y, layer, energy (inputs) and cluster_id,
- * is_seed (outputs) are HOST arrays of n entries (pinned memory gives
- * asynchronous copies); the caller keeps all six valid until the event's
- * clue_server_wait returns.  *ticket identifies the event.  Errors:
+ * is_seed (outputs) are arrays of n entries in host or device memory (host
+ * memory should be pinned: pageable memory makes the copies synchronous);
+ * the caller keeps all six valid until the event's clue_server_wait returns.
+ * *ticket identifies the event.  Errors:
  * CLUE_ERR_ARG (null pointers, n < 0, n above region_hits or the budget:
  * nothing queued), CLUE_ERR_STATE (the server is stopping). */
 int clue_server_submit(clue_server *server, const float *x, const float *y,
@@ -364,7 +365,7 @@ int clue_server_submit(clue_server *server, const float *x, const float *y,
  * arrays.  timeout_s < 0 waits without limit.  Returns CLUE_OK once it is
  * done, with the event's outcome in *status (CLUE_OK, or CLUE_ERR_INPUT /
  * CLUE_ERR_TIMEOUT raised on the device by its batch, or CLUE_ERR_CUDA) and
- * *latency_ms from submission to the results in host memory (either may be
+ * *latency_ms from submission to the results in its output arrays (either may be
  * NULL); the ticket is then released.  Returns CLUE_ERR_TIMEOUT, the ticket
  * kept, if the event is not done in time; CLUE_ERR_ARG for an unknown or
  * released ticket. */

@@ -3,7 +3,8 @@
 //
 // The backend keeps n_regions device regions of region_hits hits (inputs and
 // outputs).  An admitted event's inputs are copied from the caller's host
-// arrays into the region being filled, on a copy stream; a launched region is
+// arrays into the region being filled, on that region's copy stream (so the
+// copies of different regions can use different copy engines); a launched region is
 // one clue_run_batch on the compute stream (after the region's copies), then
 // each event's results are copied into the caller's host output arrays, the
 // batch's device error word is read back, and a host callback on the stream
@@ -37,6 +38,7 @@ class CudaBackend : public clue_serve::Backend {
         float *x = nullptr, *y = nullptr, *e = nullptr;
         int32_t *l = nullptr, *cid = nullptr;
         uint8_t *seed = nullptr;
+        cudaStream_t copy = nullptr;  // the region's input copies (regions overlap theirs)
         cudaEvent_t staged = nullptr;
     };
 
@@ -45,7 +47,7 @@ class CudaBackend : public clue_serve::Backend {
     int nreg = 0;
     float prm[4] = {};
     clue_ctx *ctx = nullptr;
-    cudaStream_t compute = nullptr, copy = nullptr;
+    cudaStream_t compute = nullptr;
     std::vector<Region> regs;
     std::vector<Callback> cbs;     // one per region: a region runs one batch at a time
     unsigned *err_host = nullptr;  // pinned, one word per region
@@ -59,7 +61,7 @@ class CudaBackend : public clue_serve::Backend {
         Region &g = regs[region];
         void *dst[4] = {g.x + off, g.y + off, g.l + off, g.e + off};
         for (int k = 0; k < 4; ++k)
-            if (cudaMemcpyAsync(dst[k], r.in[k], (size_t)r.n * 4, cudaMemcpyDefault, copy) !=
+            if (cudaMemcpyAsync(dst[k], r.in[k], (size_t)r.n * 4, cudaMemcpyDefault, g.copy) !=
                 cudaSuccess)
                 return CLUE_ERR_CUDA;
         return CLUE_OK;
@@ -69,7 +71,7 @@ class CudaBackend : public clue_serve::Backend {
                const std::vector<clue_serve::Request> &reqs, int64_t batch) override {
         if (cudaSetDevice(device) != cudaSuccess) return CLUE_ERR_CUDA;
         Region &g = regs[region];
-        if (cudaEventRecord(g.staged, copy) != cudaSuccess ||
+        if (cudaEventRecord(g.staged, g.copy) != cudaSuccess ||
             cudaStreamWaitEvent(compute, g.staged, 0) != cudaSuccess)
             return CLUE_ERR_CUDA;
         const int rc = clue_run_batch(ctx, g.x, g.y, g.l, g.e, offs.data(),
@@ -110,10 +112,11 @@ class CudaBackend : public clue_serve::Backend {
     void release() {
         cudaSetDevice(device);
         if (compute) cudaStreamSynchronize(compute);
-        if (copy) cudaStreamSynchronize(copy);
         for (Region &g : regs) {
+            if (g.copy) cudaStreamSynchronize(g.copy);
             if (g.x) cudaFree(g.x);
             if (g.staged) cudaEventDestroy(g.staged);
+            if (g.copy) cudaStreamDestroy(g.copy);
         }
         regs.clear();
         if (ctx) clue_destroy(ctx);
@@ -121,8 +124,7 @@ class CudaBackend : public clue_serve::Backend {
         if (err_host) cudaFreeHost(err_host);
         err_host = nullptr;
         if (compute) cudaStreamDestroy(compute);
-        if (copy) cudaStreamDestroy(copy);
-        compute = copy = nullptr;
+        compute = nullptr;
     }
 };
 
@@ -170,8 +172,7 @@ int clue_server_create(clue_server **out, const clue_opts *opts, const clue_serv
         return rc;
     };
     if (cudaSetDevice(be.device) != cudaSuccess) return fail(CLUE_ERR_CUDA);
-    if (cudaStreamCreateWithFlags(&be.compute, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&be.copy, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&be.compute, cudaStreamNonBlocking) != cudaSuccess)
         return fail(CLUE_ERR_CUDA);
     clue_opts o = *opts;
     o.stream = be.compute;
@@ -196,7 +197,8 @@ int clue_server_create(clue_server **out, const clue_opts *opts, const clue_serv
         g.e = (float *)(p + 3 * a4);
         g.cid = (int32_t *)(p + 4 * a4);
         g.seed = (uint8_t *)(p + 5 * a4);
-        if (cudaEventCreateWithFlags(&g.staged, cudaEventDisableTiming) != cudaSuccess)
+        if (cudaEventCreateWithFlags(&g.staged, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&g.copy, cudaStreamNonBlocking) != cudaSuccess)
             return fail(CLUE_ERR_CUDA);
     }
     s->sched = new (std::nothrow) clue_serve::Scheduler(

@@ -7,9 +7,10 @@ being filled while the region has room and the memory budget covers it (else
 the request waits), copies its inputs there at once on a copy stream, and
 launches a filled region as one ``clue_run_batch`` as soon as fewer than
 ``max_inflight`` batches are queued on the device; results are copied back
-into each request's own pinned host arrays and a stream callback marks it
-done (no polling).  Each event's result is the same whether it runs alone or
-in any batch.  Latency runs from ``submit`` to the results in host memory.
+into each request's own output arrays (host or device) and a stream callback
+marks it done (no polling).  Each event's result is the same whether it runs
+alone or in any batch.  Latency runs from ``submit`` to the results in the
+request's output arrays.
 
 This module only marshals arguments: scheduling, copies and clustering all
 run in libclue.  The scheduler itself (serve_core.cpp) is tested on a CPU
@@ -63,25 +64,21 @@ def _lib():
 
 class Ticket:
     """One submitted event.  ``result()`` waits for it and returns its
-    (cluster_id int32, is_seed uint8) host arrays."""
+    (cluster_id int32, is_seed uint8) output arrays."""
 
     def __init__(self, server, ticket, keep, cid, seed):
         self._srv, self._t, self._keep = server, ticket, keep
         self._cid, self._seed = cid, seed
-        self._done, self.latency_ms = False, None
+        self._done, self.latency_ms, self._rc = False, None, 0
 
     def result(self, timeout=None):
         if not self._done:
-            lat, st = ctypes.c_double(0.0), ctypes.c_int32(0)
-            rc = _lib().clue_server_wait(self._srv._h, self._t,
-                                         -1.0 if timeout is None else float(timeout),
-                                         ctypes.byref(st), ctypes.byref(lat))
+            rc, st, lat = self._srv.wait_raw(self._t, timeout)
             if rc == clue.CLUE_ERR_TIMEOUT:
                 raise TimeoutError(f"event not done within {timeout} s")
             if rc:
                 raise clue.ClueError(rc, "clue_server_wait")
-            self._done, self._keep, self.latency_ms = True, None, lat.value
-            self._rc = st.value
+            self._done, self._keep, self.latency_ms, self._rc = True, None, lat, st
         if self._rc:
             raise clue.ClueError(self._rc, "served event")
         return self._cid, self._seed
@@ -114,10 +111,13 @@ class Server:
             raise clue.ClueError(rc, "clue_server_create")
         self._h = h.value
         self.capacity = int(region_hits)
+        self.device = torch.device("cuda", device)
 
-    def submit(self, x, y, layer, energy) -> Ticket:
-        """Queue one event (host arrays; pinned torch tensors give
-        asynchronous copies).  Raises ValueError for an event the server
+    def submit(self, x, y, layer, energy, out=None) -> Ticket:
+        """Queue one event: host arrays (numpy, or torch CPU tensors; pinned
+        ones give asynchronous copies).  The results go to `out` = (cluster_id,
+        is_seed) arrays or tensors, host or device, else to new CUDA tensors
+        on the server's device.  Raises ValueError for an event the server
         cannot take (larger than a region or the memory budget)."""
         t = self.torch
         keep, ptrs = [], []
@@ -131,17 +131,34 @@ class Server:
                 ptrs.append(a.ctypes.data)
             keep.append(a)
         n = int(len(keep[0]))
-        cid = t.empty(n, dtype=t.int32, pin_memory=True)
-        seed = t.empty(n, dtype=t.uint8, pin_memory=True)
+        if out is None:
+            out = (t.empty(n, dtype=t.int32, device=self.device),
+                   t.empty(n, dtype=t.uint8, device=self.device))
+        cid, seed = out
         keep += [cid, seed]
+        ptr = lambda a: a.data_ptr() if isinstance(a, t.Tensor) else a.ctypes.data
+        tk = self.submit_raw(*ptrs, n, ptr(cid), ptr(seed))
+        return Ticket(self, tk, keep, cid, seed)
+
+    def submit_raw(self, x, y, layer, energy, n, cluster_id, is_seed) -> int:
+        """clue_server_submit on raw pointers (ints); returns the ticket.  The
+        caller keeps all six arrays alive until wait_raw reports the event."""
         tk = ctypes.c_int64(0)
-        rc = _lib().clue_server_submit(self._h, *ptrs, n, cid.data_ptr(), seed.data_ptr(),
-                                       ctypes.byref(tk))
+        rc = _lib().clue_server_submit(self._h, x, y, layer, energy, int(n), cluster_id,
+                                       is_seed, ctypes.byref(tk))
         if rc == clue.CLUE_ERR_ARG:
             raise ValueError(f"event of {n} hits exceeds the server's capacity")
         if rc:
             raise clue.ClueError(rc, "clue_server_submit")
-        return Ticket(self, tk.value, keep, cid.numpy(), seed.numpy())
+        return tk.value
+
+    def wait_raw(self, ticket, timeout=None):
+        """clue_server_wait: (return code, the event's status, latency ms)."""
+        lat, st = ctypes.c_double(0.0), ctypes.c_int32(0)
+        rc = _lib().clue_server_wait(self._h, int(ticket),
+                                     -1.0 if timeout is None else float(timeout),
+                                     ctypes.byref(st), ctypes.byref(lat))
+        return rc, st.value, lat.value
 
     def stats(self) -> dict:
         lib = _lib()
@@ -159,7 +176,7 @@ class Server:
             "mean_ms": float(lat.mean()) if n else None,
             "mhits_per_s": out[1] / span / 1e6 if span > 0 else None,
             "mean_events_per_batch": out[5],
-            "latency": "submit to results in host memory",
+            "latency": "submit to results in the request's output arrays",
         }
 
     def reset_stats(self):
@@ -180,19 +197,45 @@ class Server:
 
 def offered_load(server, pool, rate_events_per_s: float, n_requests: int, seed=0):
     """Submit n_requests events drawn from `pool` (list of (x, y, layer,
-    energy) tuples) at Poisson arrival times, then wait for all; returns the
-    tickets."""
+    energy) host tensors, pinned for asynchronous copies) at Poisson arrival
+    times, then wait for all; returns the latencies (ms).  The results go to
+    a ring of device buffers (four regions' worth of hits), so the driver
+    allocates nothing per request and submits fast enough for tens of
+    thousands of events per second; before a slice of the ring is reused, the
+    events still writing into it are waited for."""
+    from collections import deque
+    t = server.torch
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_events_per_s, n_requests)
     order = rng.integers(0, len(pool), n_requests)
+    src = [(x.data_ptr(), y.data_ptr(), l.data_ptr(), e.data_ptr(), int(x.numel()))
+           for x, y, l, e in pool]
+    ring_n = 4 * server.capacity
+    cid = t.empty(ring_n, dtype=t.int32, device=server.device)
+    sd = t.empty(ring_n, dtype=t.uint8, device=server.device)
+    c0, s0 = cid.data_ptr(), sd.data_ptr()
+    at, lat, pending = 0, [], deque()  # pending: (ticket, first slot, hits), ring order
+
+    def finish():
+        tk, _, _ = pending.popleft()
+        rc, st, ms = server.wait_raw(tk)
+        if rc or st:
+            raise clue.ClueError(rc or st, "served event")
+        lat.append(ms)
+
     t_next = time.perf_counter()
-    tickets = []
     for k in range(n_requests):
         t_next += gaps[k]
         dt = t_next - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
-        tickets.append(server.submit(*pool[order[k]]))
-    for tk in tickets:
-        tk.result()
-    return tickets
+        xp, yp, lp, ep, n = src[order[k]]
+        if at + n > ring_n:
+            at = 0
+        while pending and pending[0][1] < at + n and at < pending[0][1] + pending[0][2]:
+            finish()  # the oldest event still writes where this one will
+        pending.append((server.submit_raw(xp, yp, lp, ep, n, c0 + 4 * at, s0 + at), at, n))
+        at += n
+    while pending:
+        finish()
+    return lat

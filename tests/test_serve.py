@@ -5,8 +5,8 @@ serve_core.cpp, the same code the GPU server runs) over a fake device
 (tests/serve_fake.cpp, built here with g++): every request gets its own
 result, requests are batched, the memory budget gates admission, oversized
 requests are rejected, late arrivals join the next batch, nothing is lost at
-shutdown.  On the GPU: every served result against the oracle's clustering of
-the event alone.
+shutdown.  On the GPU: every served result (to host or device arrays) against
+the oracle's clustering of the event alone.
 """
 from __future__ import annotations
 
@@ -205,15 +205,22 @@ def test_served_results_equal_events_alone():
     events = [gen.make_event(n, 100, 3000 + k, "blobs") for k, n in enumerate(sizes)]
     srv = Server(device=0, extent=gen.EXTENT, max_layers=100, params=gen.PARAMS_BLOBS,
                  region_hits=1_500_000, n_regions=3, max_events_per_batch=16)
-    tickets = [srv.submit(ev.x, ev.y, ev.layer, ev.energy) for ev in events]
+    # results to pinned host arrays for half the events, to device tensors
+    # (the default) for the other half
+    outs = [(torch.empty(ev.n, dtype=torch.int32, pin_memory=True),
+             torch.empty(ev.n, dtype=torch.uint8, pin_memory=True)) if k % 2 else None
+            for k, ev in enumerate(events)]
+    tickets = [srv.submit(ev.x, ev.y, ev.layer, ev.energy, out=o)
+               for ev, o in zip(events, outs)]
     results = [t.result(timeout=120) for t in tickets]
     st = srv.stats()
     srv.close()
     assert st["batches"] < len(events)  # events really were batched
-    for ev, (cid, seed) in zip(events, results):
+    for k, (ev, (cid, seed)) in enumerate(zip(events, results)):
+        assert cid.is_cuda == (k % 2 == 0)
         ref = oracle.run_event(ev, gen.PARAMS_BLOBS, 100)
-        assert np.array_equal(cid, ref["cluster_id"])
-        assert np.array_equal(seed, ref["is_seed"])
+        assert np.array_equal(cid.cpu().numpy(), ref["cluster_id"])
+        assert np.array_equal(seed.cpu().numpy(), ref["is_seed"])
 
 
 @pytest.mark.gpu
@@ -246,8 +253,8 @@ def test_served_stream_up_to_2M_hit_events():
     for k, (cid, seed) in results:
         if k not in refs:
             refs[k] = oracle.run_event(events[k], gen.PARAMS_BLOBS, 100)
-        assert np.array_equal(cid, refs[k]["cluster_id"]), f"event {k}"
-        assert np.array_equal(seed, refs[k]["is_seed"]), f"event {k}"
+        assert np.array_equal(cid.cpu().numpy(), refs[k]["cluster_id"]), f"event {k}"
+        assert np.array_equal(seed.cpu().numpy(), refs[k]["is_seed"]), f"event {k}"
     assert max(sizes) == 2_000_000
 
 
@@ -273,4 +280,31 @@ def test_served_event_with_bad_input_fails_alone_later_events_succeed():
     good = gen.make_event(3000, 10, 2, "blobs")
     cid, _ = srv.submit(good.x, good.y, good.layer, good.energy).result(timeout=60)
     srv.close()
+    cid = cid.cpu().numpy()
     assert (cid >= -1).all() and (cid >= 0).any()
+
+
+@pytest.mark.gpu
+def test_offered_load_driver_on_gpu():
+    """The benchmark's load driver: Poisson submissions of pinned pool events
+    whose results go to a reused ring of device buffers (small regions, so the
+    ring wraps many times); every request completes and the counters agree."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_09761_gb300 import build
+    from paper_2001_09761_gb300.serve import Server, offered_load
+    build.build()
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    pool = []
+    for k, n in enumerate([3000, 20000, 70000, 150000]):
+        ev = gen.make_event(n, 100, 40 + k, "blobs")
+        pool.append((pin(ev.x), pin(ev.y), pin(ev.layer), pin(ev.energy)))
+    srv = Server(device=0, extent=gen.EXTENT, max_layers=100, params=gen.PARAMS_BLOBS,
+                 region_hits=400_000, n_regions=3)
+    lat = offered_load(srv, pool, rate_events_per_s=20_000.0, n_requests=400, seed=2)
+    st = srv.stats()
+    srv.close()
+    assert len(lat) == 400 and min(lat) > 0
+    assert st["events"] == 400 and st["batches"] < 400
+    assert st["p99_ms"] >= st["p50_ms"] > 0
