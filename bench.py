@@ -179,6 +179,8 @@ ALG_BYTES = {
     "fill_canon": 4 + 16 + 16 + 4,     # id, packed record in; sorted hit, layer out
     "rho": 16 + 4 + 4,                 # x, y, w, id, layer in; rho out
     "nh_delta": 16 + 4 + 4 + 8,        # x, y, rho, id, layer in; code, (delta^2, nh) out
+    "density": 16 + 4 + 4 + 4 + 4 + 8,  # x, y, w, layer, id in; rho, code, (delta^2, nh) out
+    "nh_rest": 0,                      # nothing unless a tile is dense or its band too long
     "link": 4 + 4 + 4 + 1,             # code, seed rank in; id, seed flag out
     "assign": 4 + 4 + 4 + 1,           # code, the nh's code, seed bits in; id, seed flag out
     "expand_level": 8 + 4 + 4 + 4,     # list range, parent id, follower in; id out
@@ -196,7 +198,7 @@ ALG_BYTES = {
 STAGED_BYTES = {"S1": 16, "S2": 16, "S3": 24, "S4": 21, "S5": 8}
 STEP_OF_KERNEL = {"fill_layers": "S1", "fill_place": "S1", "fill_cells": "S1",
                   "fill_count": "S1", "fill_scatter": "S1", "fill_canon": "S1",
-                  "rho": "S2", "nh_delta": "S3", "density": "S2+S3",
+                  "rho": "S2", "nh_delta": "S3", "density": "S2+S3", "nh_rest": "S3",
                   "scan_hits": "S4", "link": "S4", "assign": "S4+S5",
                   "expand_level": "S5", "complete": "S5", "jump": "S5"}
 COMPULSORY_BYTES = 21
@@ -475,6 +477,27 @@ def main():
     frontier_value = N / (f0.elapsed_time(f1) / 10 * 1e-3) / 1e6
     cl_f.close()
 
+    # ---- the same batch with the separate rho and nh kernels ---------------
+    cl_s = clue.Clusterer(device=local, extent=gen.EXTENT, max_layers=100,
+                          density=clue.CLUE_DENSITY_SEPARATE)
+    cl_s.tuning = tuning
+    cl_s.set_profiling(True)
+    for _ in range(3):
+        cl_s.run_batch(tx, ty, tl, te, offs, PARAMS, out=(cid, seed))
+    cl_s.sync()
+    sep_kern = {}
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(cl_s.stream)
+    for i in range(10):
+        cl_s.run_batch(tx, ty, tl, te, offs, PARAMS, out=(cid, seed))
+        if i:
+            for k, v in cl_s.kernel_times(back=1).items():
+                sep_kern[k] = sep_kern.get(k, 0.0) + v / 9
+    g1.record(cl_s.stream)
+    g1.synchronize()
+    separate_value = N / (g0.elapsed_time(g1) / 10 * 1e-3) / 1e6
+    cl_s.close()
+
     # ---- per-event launches (same events, one clue_run each) -------------
     # default options: each timed event is new to the context (warm-up uses
     # other events of the batch), as in a stream of incoming events
@@ -585,6 +608,9 @@ def main():
                            "launch to sync"}
         frontier = {"value": frontier_value, "unit": "Mhits/s",
                     "kind": "same batch, CLUE_EXPAND_FRONTIER"}
+        separate = {"value": separate_value, "unit": "Mhits/s",
+                    "kind": "same batch, CLUE_DENSITY_SEPARATE (rho kernel, then nh kernel)",
+                    "rho_ms": sep_kern.get("rho"), "nh_ms": sep_kern.get("nh_delta")}
         e2e = {"value": e2e_value, "unit": "Mhits/s", "h2d_bytes_per_step": 16 * N,
                "d2h_bytes_per_step": 5 * N, "matches_device_path": ok}
         # the compact view of every figure, last on the line so a kept tail of
@@ -592,6 +618,7 @@ def main():
         summary = {"batched_mhits_per_s": value, "e2e_mhits_per_s": e2e_value,
                    "per_event_mhits_per_s": per_event_value,
                    "frontier_mhits_per_s": frontier_value,
+                   "separate_density_mhits_per_s": separate_value,
                    "event_latency_ms_p50_p99": [latency["p50"], latency["p99"]],
                    "dominant_kernel": dom, "dominant_frac_of_hbm": roofline["frac"],
                    "step_frac_compulsory_21B": roofline["step_frac_compulsory_21B"]}
@@ -620,6 +647,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched_frontier_expansion": frontier,
+            "batched_separate_density": separate,
             "per_event": per_event,
             "latency_ms": latency,
             "summary": summary,

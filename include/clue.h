@@ -99,6 +99,11 @@ typedef struct clue_opts {
                             the 40 rounds that cover any chain.  A hit whose chain
                             needs more gets -1 and the next clue_sync returns
                             CLUE_ERR_TIMEOUT (the device never waits unbounded) */
+    int32_t density;     /* kernels of rho (Eq. 3) and nh / delta (Eq. 4), identical
+                            results: CLUE_DENSITY_FUSED (default) = one kernel per
+                            tile of hits computes rho, nh and the decision (rho of
+                            the tile's halo computed again per tile);
+                            CLUE_DENSITY_SEPARATE = a rho kernel, then an nh kernel */
 } clue_opts;
 
 #define CLUE_CHI_FLAT 0
@@ -108,9 +113,12 @@ typedef struct clue_opts {
 #define CLUE_EXPAND_FRONTIER 0
 #define CLUE_EXPAND_CHASE 1
 
+#define CLUE_DENSITY_FUSED 0
+#define CLUE_DENSITY_SEPARATE 1
+
 /* Defaults: device 0, extent [-250, 250]^2, 128 layers, tuned bin/block,
  * graphs on, own stream, expansion by chasing (CLUE_EXPAND_CHASE), flat chi
- * (Eq. 3, Algorithm 1), no scratch or walk limit. */
+ * (Eq. 3, Algorithm 1), no scratch or walk limit, fused density kernel. */
 void clue_default_opts(clue_opts *opts);
 
 /* Create a context on opts->device.  *out receives the context.  The

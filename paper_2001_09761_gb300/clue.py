@@ -41,10 +41,12 @@ class ClueOpts(ctypes.Structure):
                 ("block_size", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("expand", ctypes.c_int32),
                 ("chi", ctypes.c_int32), ("chi_param", ctypes.c_float),
-                ("max_scratch_bytes", ctypes.c_int64), ("walk_limit", ctypes.c_int32)]
+                ("max_scratch_bytes", ctypes.c_int64), ("walk_limit", ctypes.c_int32),
+                ("density", ctypes.c_int32)]
 
 
 CLUE_EXPAND_FRONTIER, CLUE_EXPAND_CHASE = 0, 1
+CLUE_DENSITY_FUSED, CLUE_DENSITY_SEPARATE = 0, 1
 CLUE_CHI_FLAT, CLUE_CHI_GAUSSIAN, CLUE_CHI_EXPONENTIAL = 0, 1, 2
 
 
@@ -210,8 +212,8 @@ def clue_stage_times(ctx, back=0):
 STAGE_OF = {"fill_layers": "grid_fill", "scan_segs": "grid_fill", "fill_place": "grid_fill",
             "fill_cells": "grid_fill",
             "fill_count": "grid_fill", "scan_cells": "grid_fill", "fill_scatter": "grid_fill",
-            "fill_canon": "grid_fill", "rho": "rho",
-            "nh_delta": "nh_delta",
+            "fill_canon": "grid_fill", "rho": "density", "nh_delta": "density",
+            "density": "density", "nh_rest": "density",
             "scan_hits": "decide_followers", "link": "decide_followers", "assign": "expand",
             "expand_level": "expand", "complete": "expand", "jump": "expand"}
 
@@ -269,7 +271,8 @@ class Clusterer:
                  max_layers: int = 128, bin_size: float = 0.0, block_size: int = 0,
                  use_graphs: bool = True, expand: int = CLUE_EXPAND_CHASE,
                  chi: int = CLUE_CHI_FLAT, chi_param: float = 0.0,
-                 max_scratch_bytes: int = 0, walk_limit: int = 0):
+                 max_scratch_bytes: int = 0, walk_limit: int = 0,
+                 density: int = CLUE_DENSITY_FUSED):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -287,6 +290,7 @@ class Clusterer:
         o.chi_param = float(chi_param)
         o.max_scratch_bytes = int(max_scratch_bytes)
         o.walk_limit = int(walk_limit)
+        o.density = int(density)
         self.max_layers = max_layers
         self.ctx = clue_create(o)
         self._last_n = 0

@@ -165,6 +165,7 @@ Params make_params(const clue_ctx *ctx, float dc, float rhoc, float delta_c, flo
     p.chi_inv = p.chi == CLUE_CHI_GAUSSIAN ? 1.0f / (2.0f * (sp * sp))
               : p.chi == CLUE_CHI_EXPONENTIAL ? 1.0f / sp : 1.0f;
     p.walk_limit = ctx->opts.walk_limit > 0 ? ctx->opts.walk_limit : INT_MAX;
+    p.fused = ctx->opts.density == CLUE_DENSITY_FUSED;
     return p;
 }
 
@@ -270,6 +271,7 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t E, int64_t
     b.front_a = b.perm;  // the first frontier reuses the grid fill's scratch
     b.jlink = b.fcount;  // pointer jumping: after the scan (frontier) or unused (chase)
     b.jlist = b.seed_list;
+    b.rest = b.seed_list;  // the fused density kernel's left tiles, before any expansion
     b.sid = b.tmp;
     const int64_t parts =
         std::max({scan_partials_needed(N), scan_partials_needed(C), scan_partials_needed(ntb)}) + 1;
@@ -363,14 +365,37 @@ int upload_tables_async(clue_ctx *ctx, const Plan &plan) {
     return CLUE_OK;
 }
 
+// The density kernels' staging capacity for a run: a tile's band holds its
+// own hits and about a window's height of grid rows around them, so the
+// expected band of an event is its tile length plus (window rows) x (hits per
+// grid row, from the event's mean over max_layers layers), with a quarter in
+// reserve; the largest over the run's events, within [BAND_CAP_MIN,
+// BAND_CAP_MAX].  Tiles whose band is larger take the per-hit or warp forms.
+int band_cap_for(const clue_ctx *ctx, const Plan &plan, const Params &p) {
+    const double r = std::max(p.rwin_rho, p.rwin_nh);
+    double most = 0.0;
+    for (const EventDesc &d : plan.ev) {
+        if (d.n <= 0) continue;
+        const double s = 1.0 / d.inv_s;
+        const double rows = std::ceil(2.0 * r / s) + 1.0;
+        const double per_row = (double)d.n / ((double)ctx->opts.max_layers * d.nby);
+        const double tlen = std::min<double>(d.n, ctx->tile_len[class_of(d.n)]);
+        most = std::max(most, 1.25 * (tlen + rows * per_row));
+    }
+    const int cap = (int)std::ceil(most / 256.0) * 256;
+    return std::min(BAND_CAP_MAX, std::max(BAND_CAP_MIN, cap));
+}
+
 // The density kernels run one CTA per tile.  Unless the options or the
 // tuning table fix their block size, a run with at least a tile per SM uses
-// 256 threads (four CTAs per SM, as their shared memory allows), a smaller
-// one 1024 (one hit per thread: its few tiles' hits all in flight at once).
-LaunchCfg make_cfg(const clue_ctx *ctx, int64_t ntiles) {
+// 256 threads (four CTAs per SM, as their shared memory allows with the
+// smallest staging capacity; two CTAs of 512 threads when the staging is
+// larger), a smaller one 1024 (one hit per thread: its few tiles' hits all in
+// flight at once).
+LaunchCfg make_cfg(const clue_ctx *ctx, int64_t ntiles, int band_cap) {
     LaunchCfg c;
     c.block_fill = 256;
-    const int automatic = ntiles >= ctx->num_sms ? 256 : 1024;
+    const int automatic = ntiles < ctx->num_sms ? 1024 : band_cap > BAND_CAP_MIN ? 512 : 256;
     c.block_density = ctx->opts.block_size > 0 ? ctx->opts.block_size
                     : ctx->block_density > 0   ? ctx->block_density
                                                : automatic;
@@ -431,10 +456,17 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
         CK(rec("fill_canon"));
     }
     nl += 3;
-    CK(launch_rho(b, p, cfg, s));
-    CK(rec("rho"));
-    CK(launch_nh(b, p, cfg, s));
-    CK(rec("nh_delta"));
+    if (p.fused) {
+        CK(launch_density(b, p, cfg, s));
+        CK(rec("density"));
+        CK(launch_nh_rest(b, p, cfg, s));
+        CK(rec("nh_rest"));
+    } else {
+        CK(launch_rho(b, p, cfg, s));
+        CK(rec("rho"));
+        CK(launch_nh(b, p, cfg, s));
+        CK(rec("nh_delta"));
+    }
     CK(launch_scan_hits(b, p, cfg, s, &nl));
     CK(rec("scan_hits"));
     if (p.chase) {
@@ -617,8 +649,9 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     b.cid = cid;
     b.is_seed = is_seed;
     b.ctrl = ctx->d_ctrl;
-    const Params p = make_params(ctx, dc, rhoc, delta_c, delta_o);
-    const LaunchCfg cfg = make_cfg(ctx, (int64_t)plan.tiles.size());
+    Params p = make_params(ctx, dc, rhoc, delta_c, delta_o);
+    p.band_cap = band_cap_for(ctx, plan, p);
+    const LaunchCfg cfg = make_cfg(ctx, (int64_t)plan.tiles.size(), p.band_cap);
 
     const bool graphs = allow_graph && ctx->opts.use_graphs && ctx->stream != nullptr;
     if (graphs) {
@@ -748,6 +781,7 @@ void clue_default_opts(clue_opts *o) {
     o->chi_param = 0.0f;
     o->max_scratch_bytes = 0;
     o->walk_limit = 0;
+    o->density = CLUE_DENSITY_FUSED;
 }
 
 int clue_create(clue_ctx **out, const clue_opts *opts) {
@@ -761,6 +795,7 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
         (o.expand != CLUE_EXPAND_FRONTIER && o.expand != CLUE_EXPAND_CHASE) ||
         o.chi < CLUE_CHI_FLAT || o.chi > CLUE_CHI_EXPONENTIAL || o.max_scratch_bytes < 0 ||
         o.walk_limit < 0 ||
+        (o.density != CLUE_DENSITY_FUSED && o.density != CLUE_DENSITY_SEPARATE) ||
         (o.chi != CLUE_CHI_FLAT && !(o.chi_param > 0.0f && std::isfinite(o.chi_param))))
         return CLUE_ERR_ARG;
     clue_ctx *ctx = new (std::nothrow) clue_ctx();
@@ -785,6 +820,7 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
     e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
     if (e != cudaSuccess) return fail(e, "cudaDeviceGetAttribute");
     e = fill_prepare();
+    if (e == cudaSuccess) e = density_prepare();
     if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute");
     if (o.stream) {
         ctx->stream = (cudaStream_t)o.stream;

@@ -16,6 +16,13 @@ constexpr int TILE = 1024;
 constexpr int SEG_MAX_LAYERS = 1024;
 constexpr int SEG_MAX_CELLS = 16384;
 
+// Candidates the density kernels stage per tile (16 bytes each): a launch's
+// capacity (Params::band_cap) lies in [BAND_CAP_MIN, BAND_CAP_MAX], chosen per
+// run from the grid's expected hits per row.  BAND_CAP_MIN keeps a CTA's
+// shared memory within the default 48 KB.
+constexpr int BAND_CAP_MIN = 1792;
+constexpr int BAND_CAP_MAX = 6144;
+
 // Cluster id of a follower whose id has not been passed down yet (frontier
 // expansion).
 constexpr int32_t PENDING = -2;
@@ -65,6 +72,7 @@ struct Ctrl {
     unsigned overflow;   // the expansion left nodes for the completion pass
     int32_t fsize[3];    // frontier sizes, rotating over the expansion levels
     int32_t npend;       // hits the bounded walk left pending (pointer jumping)
+    int32_t nrest;       // tiles the fused density kernel left for k_nh_rest
 };
 
 // Runtime parameters of one run (all events share them).
@@ -81,6 +89,8 @@ struct Params {
     int32_t chi;     // density kernel: 0 flat, 1 Gaussian, 2 exponential
     float chi_inv;   // 1 / (2 s^2) (Gaussian) or 1 / s (exponential)
     int32_t walk_limit;  // most steps of a hit's id walk: bounded walk + jump rounds
+    int32_t fused;       // 1: rho, nh and the decision in one kernel (k_density)
+    int32_t band_cap;    // staged candidates per tile of the density kernels
 };
 
 // Device pointers of one run, carved from the scratch arena.
@@ -151,6 +161,8 @@ struct Buffers {
                          //     hit (aliases fcount: dead once the scan has read it)
     int32_t *jlist;      // [N] the pending hits (aliases seed_list: dead after the
                          //     frontier's levels, unused in chase mode)
+    int32_t *rest;       // [ntiles] tiles the fused density kernel leaves for
+                         //     k_nh_rest (aliases seed_list, free until the decision)
     // scan scratch
     void *scan_partials; // [nblocks + 1] block sums
     int64_t scan_partials_cap;
@@ -171,6 +183,8 @@ cudaError_t launch_scan_cells(const Buffers &b, const LaunchCfg &c, cudaStream_t
 // sort.  fill_prepare raises the cell sort's shared-memory limit on the
 // current device; call it once per device before the first launch.
 cudaError_t fill_prepare();
+// The density kernels' dynamic shared-memory limit; once per device.
+cudaError_t density_prepare();
 cudaError_t launch_fill_layers(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_segs(const Buffers &b, const LaunchCfg &c, cudaStream_t s, int *launches);
 cudaError_t launch_fill_place(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
@@ -179,6 +193,8 @@ cudaError_t launch_fill_scatter(const Buffers &b, const LaunchCfg &c, cudaStream
 cudaError_t launch_fill_canon(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_rho(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_density(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_nh_rest(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s,
                              int *launches);
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);

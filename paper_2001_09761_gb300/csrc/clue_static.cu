@@ -216,6 +216,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     prm.chi = 0;
     prm.chi_inv = 1.0f;
     prm.walk_limit = INT_MAX;
+    prm.fused = 0;
+    prm.band_cap = BAND_CAP_MIN;  // within the default shared memory: no set-up needed
     LaunchCfg cfg;
     cfg.block_fill = 256;
     cfg.block_density = 128;

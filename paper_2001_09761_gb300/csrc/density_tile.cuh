@@ -30,7 +30,6 @@
 
 namespace clue {
 
-constexpr int BAND_CAP = 1792;   // staged candidates per tile (16 bytes each)
 constexpr int DT_ROWS = 3;       // window rows the sorted form walks
 constexpr int DT_BUCKETS = 64;   // work classes of the counting sort (64+ share one)
 constexpr int DENSE_MEAN = 96;   // mean window population that takes the warp form
@@ -46,7 +45,7 @@ __device__ __forceinline__ unsigned pack_row(int rel, int len) {
 __device__ __forceinline__ int row_start(unsigned w) { return (int)(short)(w & 0xffffu); }
 __device__ __forceinline__ int row_len(unsigned w) { return (int)(w >> 16); }
 
-// Per-tile shared state: 18 KB, plus the staged band (28 KB).
+// Per-tile shared state: 18 KB, plus the staged band (dynamic shared memory).
 struct DensityShared {
     uint4 win[TILE];                   // windows (pack_row x 3, candidate count)
     unsigned short perm[TILE];         // the tile's hits by descending window population
@@ -142,10 +141,11 @@ __device__ __forceinline__ void tile_windows(const Buffers &b, const Tile &tl,
     __syncthreads();
 }
 
-// Whether the sorted form takes the tile (uniform over the CTA).
-__device__ __forceinline__ bool tile_sorted(const DensityShared &sh) {
+// Whether the sorted form takes the tile (uniform over the CTA): windows of
+// at most DT_ROWS rows and a band within the launch's staging capacity.
+__device__ __forceinline__ bool tile_sorted(const DensityShared &sh, int cap) {
     return sh.rows <= DT_ROWS && sh.lo >= -DT_OUT + 1 && sh.hi <= DT_OUT - 1 &&
-           sh.hi - sh.lo <= BAND_CAP;
+           sh.hi - sh.lo <= cap;
 }
 
 // Counting sort of the tile's hits by descending window population (the
@@ -283,7 +283,7 @@ __device__ __forceinline__ void rho_tile(const Buffers &b, const Params &p, int 
         __syncthreads();  // the shared state is reused by the next tile
         return;
     }
-    if (!tile_sorted(sh)) {  // per-hit form
+    if (!tile_sorted(sh, p.band_cap)) {  // per-hit form
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
             b.rho[q] = rho_of_hit<CHI>(b, p, ev, fw, b.sp[q], b.lay_s[q]);
@@ -368,7 +368,7 @@ __device__ __forceinline__ void nh_tile(const Buffers &b, const Params &p, int t
         __syncthreads();
         return;
     }
-    if (!tile_sorted(sh)) {  // per-hit form
+    if (!tile_sorted(sh, p.band_cap)) {  // per-hit form
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
             const float4 me = b.sp[q];
@@ -384,6 +384,64 @@ __device__ __forceinline__ void nh_tile(const Buffers &b, const Params &p, int t
         const int u = tl.start + lo + h;
         const float4 r = b.sp[u];
         band[h] = make_float4(r.x, r.y, b.rho[u], __int_as_float(b.sid[u]));
+    }
+    __syncthreads();
+    if (sh.rows <= 2)
+        nh_sorted<2>(b, p, tl, sh, band);
+    else
+        nh_sorted<DT_ROWS>(b, p, tl, sh, band);
+    __syncthreads();
+}
+
+// ---- rho, nh, delta and the decision in one pass (the fused form) ----------
+//
+// One CTA per tile, with the sorted form's staging done once for both steps:
+// the windows of radius max(d_c, d_m) (a superset of both searches' windows;
+// the exact d2 tests pick the neighbours), one ordering of the tile's hits by
+// window population, one band staged.  Then rho of the tile's hits from the
+// band (written to global memory for the intermediates and for other tiles);
+// rho of the band's hits outside the tile (the halo, whose densities the
+// tile's nh needs) by a walk over their own windows in global memory, each
+// computed again by every tile whose band holds it (identical values); the
+// band restaged in place as (x, y, rho, id); nh and the decision of the
+// tile's hits.  So rho goes straight to nh with no pass over the batch in
+// between.  A tile the sorted form does not take (dense windows, a band
+// beyond the staging capacity, windows of more rows) or whose halo holds more
+// hits than the tile itself (dense neighbourhoods) gets only its rho here
+// (rho_tile's forms) and joins a list that k_nh_rest finishes after every
+// tile's rho is written.
+template <int CHI, int U>
+__device__ __forceinline__ void density_tile(const Buffers &b, const Params &p, int t,
+                                             DensityShared &sh, float4 *band) {
+    const Tile tl = b.tiles[t];
+    const EventDesc ev = b.events[tl.event];
+    const FixedW fw = fixed_weights(b.wexp + 2 * tl.event, CHI);  // uniform per event
+    tile_windows<U>(b, tl, ev, fmaxf(p.rwin_rho, p.rwin_nh), sh);
+    // fused when the windows are not dense, the band fits and its halo (whose
+    // rho is computed again here) holds at most as many hits as the tile
+    const bool fused = sh.tsum < (unsigned long long)DENSE_MEAN * tl.len &&
+                       tile_sorted(sh, p.band_cap) && sh.hi - sh.lo <= 2 * tl.len;
+    if (!fused) {
+        __syncthreads();  // every thread has read the shared state rho_tile resets
+        rho_tile<CHI, U>(b, p, t, sh, band);
+        if (threadIdx.x == 0) b.rest[atomicAdd(&b.ctrl->nrest, 1)] = t;
+        return;
+    }
+    tile_sort(tl, sh);
+    const int lo = sh.lo, n_band = sh.hi - sh.lo;
+    for (int h = threadIdx.x; h < n_band; h += blockDim.x) band[h] = b.sp[tl.start + lo + h];
+    __syncthreads();
+    if (sh.rows <= 2)
+        rho_sorted<CHI, 2>(b, p, tl, ev, fw, sh, band);
+    else
+        rho_sorted<CHI, DT_ROWS>(b, p, tl, ev, fw, sh, band);
+    __syncthreads();  // the tile's rho are written; the band's weights are no longer read
+    for (int h = threadIdx.x; h < n_band; h += blockDim.x) {
+        const int u = tl.start + lo + h;
+        const float4 r = band[h];
+        const bool in_tile = h + lo >= 0 && h + lo < tl.len;
+        const float rh = in_tile ? b.rho[u] : rho_of_hit<CHI>(b, p, ev, fw, r, b.lay_s[u]);
+        band[h] = make_float4(r.x, r.y, rh, __int_as_float(b.sid[u]));
     }
     __syncthreads();
     if (sh.rows <= 2)

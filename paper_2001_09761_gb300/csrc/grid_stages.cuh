@@ -131,6 +131,7 @@ __device__ __forceinline__ void fill_layers_stage(const Buffers &b, const Params
         b.ctrl->overflow = 0u;
         b.ctrl->fsize[0] = b.ctrl->fsize[1] = b.ctrl->fsize[2] = 0;
         b.ctrl->npend = 0;
+        b.ctrl->nrest = 0;
     }
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];

@@ -102,6 +102,15 @@ def test_parity_vs_oracle(clue_mod, kind, n, L, params, seed, ext, expand):
     assert_parity(g, ref)
 
 
+@pytest.mark.parametrize("kind,n,L,params,seed,ext", CASES)
+def test_parity_separate_density_kernels(clue_mod, kind, n, L, params, seed, ext):
+    """The separate rho and nh kernels (CLUE_DENSITY_SEPARATE) give the
+    oracle's bytes too."""
+    ev = gen.make_event(n, L, seed, kind, extent=ext)
+    cl = _cl(clue_mod, ext, L, density=clue_mod.CLUE_DENSITY_SEPARATE)
+    assert_parity(_gpu_all(cl, ev, params), oracle.run_event(ev, params, L, extent=ext))
+
+
 def test_parity_scaling_event_full_size(clue_mod):
     """100 layers x 10k hits (1M hits), the largest single event of the
     scaling sweep, compared in full."""
@@ -210,7 +219,7 @@ def test_profiled_graph_replay_keeps_each_runs_times(clue_mod):
         cl.run_batch(tx, ty, tl, te, offs, gen.PARAMS_BLOBS, out=(cid, seed))
         if r >= 1:
             prev = cl.kernel_times(back=1)  # read while run r is queued
-            assert {"fill_cells", "rho", "nh_delta", "assign"} <= set(prev)
+            assert {"fill_cells", "density", "nh_rest", "assign"} <= set(prev)
     times = [cl.kernel_times(back=k) for k in range(4)]
     for t in times:
         assert set(t) == set(times[0]) and all(v >= 0 for v in t.values())
@@ -694,10 +703,10 @@ def test_stage_times_and_launch_count(clue_mod):
         cl.set_profiling(True)
         cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_BLOBS)
         st = cl.stage_times()
-        assert list(st) == ["grid_fill", "rho", "nh_delta", "decide_followers", "expand"]
+        assert list(st) == ["grid_fill", "density", "decide_followers", "expand"]
         assert all(v >= 0 for v in st.values())
         kt = cl.kernel_times()
-        assert {"fill_cells", "rho", "nh_delta"} | last <= set(kt)
+        assert {"fill_cells", "density", "nh_rest"} | last <= set(kt)
         # two-level grid fill with a one-CTA segment scan (4); chase: one-CTA
         # seed-rank scan; both end with the pointer-jumping kernel
         assert cl.launch_count() == (4 + 20 if expand == 0 else 9)
