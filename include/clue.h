@@ -100,10 +100,12 @@ typedef struct clue_opts {
                             needs more gets -1 and the next clue_sync returns
                             CLUE_ERR_TIMEOUT (the device never waits unbounded) */
     int32_t density;     /* kernels of rho (Eq. 3) and nh / delta (Eq. 4), identical
-                            results: CLUE_DENSITY_FUSED (default) = one kernel per
-                            tile of hits computes rho, nh and the decision (rho of
-                            the tile's halo computed again per tile);
-                            CLUE_DENSITY_SEPARATE = a rho kernel, then an nh kernel */
+                            results: CLUE_DENSITY_FUSED = one kernel per tile of hits
+                            computes rho, nh and the decision (rho of the tile's
+                            halo computed again per tile); CLUE_DENSITY_SEPARATE = a
+                            rho kernel, then an nh kernel; CLUE_DENSITY_AUTO (the
+                            default) = fused where the run's grid rows are sparse
+                            enough for the smallest staging, else separate */
 } clue_opts;
 
 #define CLUE_CHI_FLAT 0
@@ -113,12 +115,13 @@ typedef struct clue_opts {
 #define CLUE_EXPAND_FRONTIER 0
 #define CLUE_EXPAND_CHASE 1
 
-#define CLUE_DENSITY_FUSED 0
-#define CLUE_DENSITY_SEPARATE 1
+#define CLUE_DENSITY_AUTO 0
+#define CLUE_DENSITY_FUSED 1
+#define CLUE_DENSITY_SEPARATE 2
 
 /* Defaults: device 0, extent [-250, 250]^2, 128 layers, tuned bin/block,
  * graphs on, own stream, expansion by chasing (CLUE_EXPAND_CHASE), flat chi
- * (Eq. 3, Algorithm 1), no scratch or walk limit, fused density kernel. */
+ * (Eq. 3, Algorithm 1), no scratch or walk limit, density kernels by run. */
 void clue_default_opts(clue_opts *opts);
 
 /* Create a context on opts->device.  *out receives the context.  The

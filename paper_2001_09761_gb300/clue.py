@@ -46,7 +46,7 @@ class ClueOpts(ctypes.Structure):
 
 
 CLUE_EXPAND_FRONTIER, CLUE_EXPAND_CHASE = 0, 1
-CLUE_DENSITY_FUSED, CLUE_DENSITY_SEPARATE = 0, 1
+CLUE_DENSITY_AUTO, CLUE_DENSITY_FUSED, CLUE_DENSITY_SEPARATE = 0, 1, 2
 CLUE_CHI_FLAT, CLUE_CHI_GAUSSIAN, CLUE_CHI_EXPONENTIAL = 0, 1, 2
 
 
@@ -272,7 +272,7 @@ class Clusterer:
                  use_graphs: bool = True, expand: int = CLUE_EXPAND_CHASE,
                  chi: int = CLUE_CHI_FLAT, chi_param: float = 0.0,
                  max_scratch_bytes: int = 0, walk_limit: int = 0,
-                 density: int = CLUE_DENSITY_FUSED):
+                 density: int = CLUE_DENSITY_AUTO):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)

@@ -102,6 +102,7 @@ struct clue_ctx {
     float bin_scale[NCLASS];
     int tile_len[NCLASS];   // hits per tile (one CTA of every per-tile kernel) per class
     int block_density = 0;  // threads per CTA of rho / nh (one CTA per tile); 0: by run size
+    int band_cap = 0;       // staged candidates per tile of the density kernels; 0: by run
     bool profiling = false;
     // ring of event sets: profiled run r stamps set r % NPSETS
     cudaEvent_t pev[NPSETS][NPROF] = {};
@@ -165,7 +166,7 @@ Params make_params(const clue_ctx *ctx, float dc, float rhoc, float delta_c, flo
     p.chi_inv = p.chi == CLUE_CHI_GAUSSIAN ? 1.0f / (2.0f * (sp * sp))
               : p.chi == CLUE_CHI_EXPONENTIAL ? 1.0f / sp : 1.0f;
     p.walk_limit = ctx->opts.walk_limit > 0 ? ctx->opts.walk_limit : INT_MAX;
-    p.fused = ctx->opts.density == CLUE_DENSITY_FUSED;
+
     return p;
 }
 
@@ -258,6 +259,7 @@ size_t carve(clue_ctx *ctx, Buffers &b, int64_t N, int64_t C, int64_t E, int64_t
     b.rec = (float4 *)take(n * 16);
     b.hr = (float2 *)b.rec;
     b.rho = (float *)take(n * 4);
+    b.spr = (float4 *)take(n * 16);
     b.front_b = (int32_t *)take(n * 4);  // the second expansion frontier
     b.code = b.key;  // the cell of each hit is dead once the cells are sorted
     b.cell16 = (unsigned short *)b.key;
@@ -382,7 +384,7 @@ int band_cap_for(const clue_ctx *ctx, const Plan &plan, const Params &p) {
         const double tlen = std::min<double>(d.n, ctx->tile_len[class_of(d.n)]);
         most = std::max(most, 1.25 * (tlen + rows * per_row));
     }
-    const int cap = (int)std::ceil(most / 256.0) * 256;
+    const int cap = ctx->band_cap > 0 ? ctx->band_cap : (int)std::ceil(most / 256.0) * 256;
     return std::min(BAND_CAP_MAX, std::max(BAND_CAP_MIN, cap));
 }
 
@@ -642,6 +644,7 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     rc = ensure_arena(ctx, need);
     if (rc) return rc;
     carve(ctx, b, plan.N, plan.C, E64, plan.nseg, plan.ntb, false);
+    b.rho_in_spr = p.fused ? 0 : 1;
     b.x = x;
     b.y = y;
     b.w = energy;
@@ -651,6 +654,10 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     b.ctrl = ctx->d_ctrl;
     Params p = make_params(ctx, dc, rhoc, delta_c, delta_o);
     p.band_cap = band_cap_for(ctx, plan, p);
+    // the fused density kernel where the run's bands fit the smallest staging
+    // (its halo recomputation is cheap there), else the separate kernels
+    p.fused = ctx->opts.density == CLUE_DENSITY_FUSED ||
+              (ctx->opts.density == CLUE_DENSITY_AUTO && p.band_cap == BAND_CAP_MIN);
     const LaunchCfg cfg = make_cfg(ctx, (int64_t)plan.tiles.size(), p.band_cap);
 
     const bool graphs = allow_graph && ctx->opts.use_graphs && ctx->stream != nullptr;
@@ -781,7 +788,7 @@ void clue_default_opts(clue_opts *o) {
     o->chi_param = 0.0f;
     o->max_scratch_bytes = 0;
     o->walk_limit = 0;
-    o->density = CLUE_DENSITY_FUSED;
+    o->density = CLUE_DENSITY_AUTO;
 }
 
 int clue_create(clue_ctx **out, const clue_opts *opts) {
@@ -795,7 +802,7 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
         (o.expand != CLUE_EXPAND_FRONTIER && o.expand != CLUE_EXPAND_CHASE) ||
         o.chi < CLUE_CHI_FLAT || o.chi > CLUE_CHI_EXPONENTIAL || o.max_scratch_bytes < 0 ||
         o.walk_limit < 0 ||
-        (o.density != CLUE_DENSITY_FUSED && o.density != CLUE_DENSITY_SEPARATE) ||
+        o.density < CLUE_DENSITY_AUTO || o.density > CLUE_DENSITY_SEPARATE ||
         (o.chi != CLUE_CHI_FLAT && !(o.chi_param > 0.0f && std::isfinite(o.chi_param))))
         return CLUE_ERR_ARG;
     clue_ctx *ctx = new (std::nothrow) clue_ctx();
@@ -1230,7 +1237,8 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
 
 int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap) {
     if (!ctx) return -CLUE_ERR_ARG;
-    std::string s = "# clue tuning v2: class <lo> <hi> <bin_scale> <tile_hits>; block <threads>\n";
+    std::string s = "# clue tuning v2: class <lo> <hi> <bin_scale> <tile_hits>; block <threads>; "
+                    "band <staged records>\n";
     char line[160];
     for (int k = 0; k < NCLASS; ++k) {
         std::snprintf(line, sizeof(line), "class %" PRId64 " %" PRId64 " %.4f %d\n", CLASS_EDGE[k],
@@ -1238,6 +1246,8 @@ int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap) {
         s += line;
     }
     std::snprintf(line, sizeof(line), "block %d\n", ctx->block_density);
+    s += line;
+    std::snprintf(line, sizeof(line), "band %d\n", ctx->band_cap);
     s += line;
     if (buf && cap > 0) {
         std::strncpy(buf, s.c_str(), (size_t)cap - 1);
@@ -1254,7 +1264,7 @@ int clue_set_tuning(clue_ctx *ctx, const char *text) {
         scale[k] = ctx->bin_scale[k];
         tlen[k] = ctx->tile_len[k];
     }
-    int block = ctx->block_density;
+    int block = ctx->block_density, band = ctx->band_cap;
     const char *p = text;
     while (*p) {
         const char *eol = std::strchr(p, '\n');
@@ -1279,6 +1289,9 @@ int clue_set_tuning(clue_ctx *ctx, const char *text) {
         } else if (std::sscanf(line.c_str(), "block %d %c", &bl, &tail) == 1) {
             if (bl != 0 && (bl < 32 || bl > 1024 || bl % 32)) return CLUE_ERR_ARG;  // 0: by run size
             block = bl;
+        } else if (std::sscanf(line.c_str(), "band %d %c", &bl, &tail) == 1) {
+            if (bl != 0 && (bl < BAND_CAP_MIN || bl > BAND_CAP_MAX)) return CLUE_ERR_ARG;
+            band = bl;  // 0: by run
         } else {
             return CLUE_ERR_ARG;
         }
@@ -1288,6 +1301,7 @@ int clue_set_tuning(clue_ctx *ctx, const char *text) {
         ctx->tile_len[k] = tlen[k];
     }
     ctx->block_density = block;
+    ctx->band_cap = band;
     drop_graphs(ctx);
     return CLUE_OK;
 }

@@ -141,7 +141,11 @@ struct Buffers {
                          //     nh step and the intermediates export)
     int32_t *lay_s;      // [N] layer in sorted order
     // density
-    float *rho;          // [N] rho by sorted position (written by the rho step)
+    float *rho;          // [N] rho by sorted position (fused density kernel)
+    float4 *spr;         // [N] x, y, rho, id by sorted position (separate density
+                         //     kernels: the rho kernel writes it, the nh kernel reads
+                         //     one record per candidate)
+    int32_t rho_in_spr;  // 1: this run's rho is in spr (separate kernels), else in rho
     float2 *hr;          // [N] by sorted position: delta^2, nh (int bits: batch index
                          //     or -1), read only by the intermediates export
     // decision / expansion

@@ -40,7 +40,7 @@ constexpr size_t STATIC_BYTES =
     al(NB * 4) /*key*/ + al(NB * 4) /*rank*/ + al(CB * 4) /*count*/ + al((CB + 1) * 4) /*cell_start*/ +
     al(NB * 4) /*perm*/ + al(NB * 4) /*tmp*/ +
     al(NB * 16) /*sp*/ + al(NB * 4) /*lay_s*/ +
-    al(NB * 16) /*rec = hr*/ + al(NB * 4) /*rho*/ + al(NB * 4) /*front_b*/ +
+    al(NB * 16) /*rec = hr*/ + al(NB * 4) /*rho*/ + al(NB * 16) /*spr*/ + al(NB * 4) /*front_b*/ +
     al(NB * 4) /*fcount*/ + al((NB + 1) * 8) /*hs*/ + al(NB * 4) /*fol*/ +
     al(NB * 4) /*seed_list*/ + al((size_t)STATIC_PARTS * 8) /*scan partials*/ + al(8) /*wexp*/;
 
@@ -150,6 +150,8 @@ extern "C" int clue_run_static(const float *x, const float *y, const int32_t *la
     b.rec = (float4 *)take(NB * 16);
     b.hr = (float2 *)b.rec;
     b.rho = (float *)take(NB * 4);
+    b.spr = (float4 *)take(NB * 16);
+    b.rho_in_spr = 1;  // the separate density kernels
     b.front_b = (int32_t *)take(NB * 4);
     b.code = b.key;
     b.fcount = (int32_t *)take(NB * 4);

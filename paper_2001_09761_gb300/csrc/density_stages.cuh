@@ -245,6 +245,24 @@ __device__ __forceinline__ unsigned long long nh_key(float d2, int j) {
     return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
 }
 
+// Sorted position u as the nh search reads it: (x, y, rho, id).  The separate
+// density kernels keep it as one record; the fused kernel's rho array and the
+// sorted records give it in three loads.
+__device__ __forceinline__ float4 nh_record(const Buffers &b, const Params &p, int64_t u) {
+    if (!p.fused) return b.spr[u];
+    const float4 r = b.sp[u];
+    return make_float4(r.x, r.y, b.rho[u], __int_as_float(b.sid[u]));
+}
+
+// Store rho of sorted position q (at x, y) where this run's nh reads it.
+__device__ __forceinline__ void store_rho(const Buffers &b, const Params &p, int64_t q, float x,
+                                          float y, float r) {
+    if (p.fused)
+        b.rho[q] = r;
+    else
+        b.spr[q] = make_float4(x, y, r, __int_as_float(b.sid[q]));
+}
+
 // nh_i by a walk over i's window in global memory (one thread per hit): over
 // the window of radius d_m, the (d2, j)-lexicographic minimum among hits with
 // d2 < d_m^2 and rho_j > rho_i (the minimum is order-free).
@@ -258,10 +276,10 @@ __device__ __forceinline__ unsigned long long nh_of_hit(const Buffers &b, const 
         const int64_t row = plane + (int64_t)by * ev.nbx;
         const int e = b.cell_start[row + w.hx + 1];
         for (int u = b.cell_start[row + w.lx]; u < e; ++u) {  // branch-free body
-            const float4 h = b.sp[u];
+            const float4 h = nh_record(b, p, u);
             const float d2 = sq_dist(xi, yi, h.x, h.y);
-            const unsigned long long k = nh_key(d2, b.sid[u]);
-            best = (b.rho[u] > ri && k < best) ? k : best;
+            const unsigned long long k = nh_key(d2, __float_as_int(h.w));
+            best = (h.z > ri && k < best) ? k : best;
         }
     }
     return best;

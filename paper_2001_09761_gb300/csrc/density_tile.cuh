@@ -239,7 +239,7 @@ __device__ __forceinline__ void rho_sorted(const Buffers &b, const Params &p, co
             r = rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv,
                               fixed ? fw.unit : 0.0f);
         }
-        b.rho[q] = r;
+        store_rho(b, p, q, me.x, me.y, r);
     }
 }
 
@@ -275,10 +275,11 @@ __device__ __forceinline__ void rho_tile(const Buffers &b, const Params &p, int 
             }
             acc = warp_sum_ll(acc);
             if (lane_id() == 0)
-                b.rho[q] = 32 - __clz(T) <= fw.budget
-                               ? __fmul_rn(__ll2float_rn(acc), fw.unit)
-                               : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2,
-                                               p.chi_inv, fw.unit);
+                store_rho(b, p, q, me.x, me.y,
+                          32 - __clz(T) <= fw.budget
+                              ? __fmul_rn(__ll2float_rn(acc), fw.unit)
+                              : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2,
+                                              p.chi_inv, fw.unit));
         }
         __syncthreads();  // the shared state is reused by the next tile
         return;
@@ -286,7 +287,8 @@ __device__ __forceinline__ void rho_tile(const Buffers &b, const Params &p, int 
     if (!tile_sorted(sh, p.band_cap)) {  // per-hit form
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
-            b.rho[q] = rho_of_hit<CHI>(b, p, ev, fw, b.sp[q], b.lay_s[q]);
+            const float4 me = b.sp[q];
+            store_rho(b, p, q, me.x, me.y, rho_of_hit<CHI>(b, p, ev, fw, me, b.lay_s[q]));
         }
         __syncthreads();
         return;
@@ -347,8 +349,7 @@ __device__ __forceinline__ void nh_tile(const Buffers &b, const Params &p, int t
         const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
         for (int k = warp; k < tl.len; k += nwarps) {
             const int q = tl.start + k;
-            const float4 me = b.sp[q];
-            const float ri = b.rho[q];
+            const float4 me = nh_record(b, p, q);  // x, y, rho, id
             const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
             const Window w = window_of(me.x, me.y, p.rwin_nh, ev);
             unsigned long long best = nh_none(p);
@@ -356,14 +357,14 @@ __device__ __forceinline__ void nh_tile(const Buffers &b, const Params &p, int t
                 const int64_t row = plane + (int64_t)by * ev.nbx;
                 const int e = b.cell_start[row + w.hx + 1];
                 for (int u = b.cell_start[row + w.lx] + lane_id(); u < e; u += 32) {
-                    const float4 h = b.sp[u];
+                    const float4 h = nh_record(b, p, u);
                     const float d2 = sq_dist(me.x, me.y, h.x, h.y);
-                    const unsigned long long key = nh_key(d2, b.sid[u]);
-                    best = (b.rho[u] > ri && key < best) ? key : best;
+                    const unsigned long long key = nh_key(d2, id_of(h));
+                    best = (h.z > me.z && key < best) ? key : best;
                 }
             }
             best = warp_min_u64(best);
-            if (lane_id() == 0) nh_store(b, p, q, b.sid[q], ri, best);
+            if (lane_id() == 0) nh_store(b, p, q, id_of(me), me.z, best);
         }
         __syncthreads();
         return;
@@ -371,20 +372,15 @@ __device__ __forceinline__ void nh_tile(const Buffers &b, const Params &p, int t
     if (!tile_sorted(sh, p.band_cap)) {  // per-hit form
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
-            const float4 me = b.sp[q];
-            const float ri = b.rho[q];
-            nh_store(b, p, q, b.sid[q], ri, nh_of_hit(b, p, ev, me.x, me.y, ri, b.lay_s[q]));
+            const float4 me = nh_record(b, p, q);
+            nh_store(b, p, q, id_of(me), me.z, nh_of_hit(b, p, ev, me.x, me.y, me.z, b.lay_s[q]));
         }
         __syncthreads();
         return;
     }
     tile_sort(tl, sh);
     const int lo = sh.lo, n_band = sh.hi - sh.lo;
-    for (int h = threadIdx.x; h < n_band; h += blockDim.x) {
-        const int u = tl.start + lo + h;
-        const float4 r = b.sp[u];
-        band[h] = make_float4(r.x, r.y, b.rho[u], __int_as_float(b.sid[u]));
-    }
+    for (int h = threadIdx.x; h < n_band; h += blockDim.x) band[h] = nh_record(b, p, tl.start + lo + h);
     __syncthreads();
     if (sh.rows <= 2)
         nh_sorted<2>(b, p, tl, sh, band);

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) k_export(Buffers b, float *rho, float *de
             const int q = tl.start + k;
             const int g = b.sid[q];
             const float2 h = b.hr[q];
-            if (rho) rho[g] = b.rho[q];
+            if (rho) rho[g] = b.rho_in_spr ? b.spr[q].z : b.rho[q];
             if (delta) delta[g] = sqrtf(h.x);
             if (nh) {
                 const int j = __float_as_int(h.y);

@@ -102,12 +102,14 @@ def test_parity_vs_oracle(clue_mod, kind, n, L, params, seed, ext, expand):
     assert_parity(g, ref)
 
 
+@pytest.mark.parametrize("density", ["FUSED", "SEPARATE"])
 @pytest.mark.parametrize("kind,n,L,params,seed,ext", CASES)
-def test_parity_separate_density_kernels(clue_mod, kind, n, L, params, seed, ext):
-    """The separate rho and nh kernels (CLUE_DENSITY_SEPARATE) give the
-    oracle's bytes too."""
+def test_parity_forced_density_kernels(clue_mod, kind, n, L, params, seed, ext, density):
+    """Both density forms, forced on every case (the default picks one per
+    run): the fused kernel, whose dense or wide tiles go to the list-driven
+    nh kernel, and the separate rho and nh kernels give the oracle's bytes."""
     ev = gen.make_event(n, L, seed, kind, extent=ext)
-    cl = _cl(clue_mod, ext, L, density=clue_mod.CLUE_DENSITY_SEPARATE)
+    cl = _cl(clue_mod, ext, L, density=getattr(clue_mod, f"CLUE_DENSITY_{density}"))
     assert_parity(_gpu_all(cl, ev, params), oracle.run_event(ev, params, L, extent=ext))
 
 
