@@ -644,7 +644,6 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     rc = ensure_arena(ctx, need);
     if (rc) return rc;
     carve(ctx, b, plan.N, plan.C, E64, plan.nseg, plan.ntb, false);
-    b.rho_in_spr = p.fused ? 0 : 1;
     b.x = x;
     b.y = y;
     b.w = energy;
@@ -658,6 +657,7 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     // (its halo recomputation is cheap there), else the separate kernels
     p.fused = ctx->opts.density == CLUE_DENSITY_FUSED ||
               (ctx->opts.density == CLUE_DENSITY_AUTO && p.band_cap == BAND_CAP_MIN);
+    b.rho_in_spr = p.fused ? 0 : 1;
     const LaunchCfg cfg = make_cfg(ctx, (int64_t)plan.tiles.size(), p.band_cap);
 
     const bool graphs = allow_graph && ctx->opts.use_graphs && ctx->stream != nullptr;
