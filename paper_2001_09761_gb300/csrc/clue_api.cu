@@ -401,6 +401,10 @@ LaunchCfg make_cfg(const clue_ctx *ctx, int64_t ntiles, int band_cap) {
     c.block_density = ctx->opts.block_size > 0 ? ctx->opts.block_size
                     : ctx->block_density > 0   ? ctx->block_density
                                                : automatic;
+    // a tuned block below 512 threads would leave a run with wide staging (two
+    // CTAs per SM) at half occupancy: such runs keep at least 512
+    if (ctx->opts.block_size == 0 && band_cap > BAND_CAP_MIN && ntiles >= ctx->num_sms)
+        c.block_density = std::max(c.block_density, 512);
     c.grid_cap = ctx->num_sms * 8;
     return c;
 }

@@ -13,13 +13,10 @@
 //    descending candidate count (a counting sort in shared memory), so the
 //    32 lanes of a warp take hits with near-equal windows, and each lane walks
 //    its window's runs as one flat loop (no per-row reconvergence);
-//  * warp form (rho with the fixed point, and nh, on tiles whose windows
-//    average DENSE_MEAN candidates or more: dense hotspots): a warp takes one
-//    hit at a time and its lanes stride over the window's runs (coalesced
-//    loads from global memory), with a warp reduction of the integer sum or
-//    of the (d2, j) key;
 //  * per-hit form otherwise (windows of more rows, bands beyond the staging
-//    capacity): one thread per hit walks its window in global memory.
+//    capacity): one thread per hit, in grid order, walks its window in global
+//    memory (neighbouring hits of dense regions have similar windows, so the
+//    lanes of a warp stay close there too).
 //
 // Every form computes the same function of the neighbour sets (the exact
 // density, the lexicographic minimum), so the form, the order of the hits and
@@ -32,7 +29,6 @@ namespace clue {
 
 constexpr int DT_ROWS = 3;       // window rows the sorted form walks
 constexpr int DT_BUCKETS = 64;   // work classes of the counting sort (64+ share one)
-constexpr int DENSE_MEAN = 96;   // mean window population that takes the warp form
 constexpr int DT_OUT = 1 << 14;  // window starts further than this from the tile
 
 // One hit's window for the sorted form: per row (up to DT_ROWS) the start
@@ -191,13 +187,6 @@ struct FlatWin {
 
 // ---- rho ---------------------------------------------------------------------
 
-// Sum of a 64-bit integer over the warp (exact).
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
-    return v;
-}
-
 // rho of the tile's hits in the sorted form (the band staged, hits ordered).
 template <int CHI, int ROWS>
 __device__ __forceinline__ void rho_sorted(const Buffers &b, const Params &p, const Tile &tl,
@@ -251,39 +240,6 @@ __device__ __forceinline__ void rho_tile(const Buffers &b, const Params &p, int 
     const FixedW fw = fixed_weights(b.wexp + 2 * tl.event, CHI);  // uniform per event
     const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
     tile_windows<U>(b, tl, ev, p.rwin_rho, sh);
-    const bool fixed = CHI == 0 && fw.on;
-    if (fixed && sh.tsum >= (unsigned long long)DENSE_MEAN * tl.len) {
-        // warp form: lanes stride over one hit's window
-        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        for (int k = warp; k < tl.len; k += nwarps) {
-            const int q = tl.start + k;
-            const float4 me = b.sp[q];
-            const int lay = b.lay_s[q];
-            const int64_t plane = ev.cell_off + (int64_t)lay * nbxy;
-            const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
-            long long acc = 0;
-            unsigned T = 0;
-            for (int by = w.ly; by <= w.hy; ++by) {
-                const int64_t row = plane + (int64_t)by * ev.nbx;
-                const int u0 = b.cell_start[row + w.lx], e = b.cell_start[row + w.hx + 1];
-                T += (unsigned)(e - u0);
-                for (int u = u0 + lane_id(); u < e; u += 32) {
-                    const float4 h = b.sp[u];
-                    const float d2 = sq_dist(me.x, me.y, h.x, h.y);
-                    acc += d2 < p.dc2 ? fixed_weight_of(h) : 0ll;
-                }
-            }
-            acc = warp_sum_ll(acc);
-            if (lane_id() == 0)
-                store_rho(b, p, q, me.x, me.y,
-                          32 - __clz(T) <= fw.budget
-                              ? __fmul_rn(__ll2float_rn(acc), fw.unit)
-                              : rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2,
-                                              p.chi_inv, fw.unit));
-        }
-        __syncthreads();  // the shared state is reused by the next tile
-        return;
-    }
     if (!tile_sorted(sh, p.band_cap)) {  // per-hit form
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
@@ -305,16 +261,6 @@ __device__ __forceinline__ void rho_tile(const Buffers &b, const Params &p, int 
 }
 
 // ---- nh, delta and the decision ----------------------------------------------
-
-// Lexicographic minimum of the 64-bit key over the warp.
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long u = __shfl_xor_sync(FULL_MASK, v, o);
-        v = u < v ? u : v;
-    }
-    return v;
-}
 
 // nh of the tile's hits in the sorted form (the band staged as x, y, rho, id).
 template <int ROWS>
@@ -344,31 +290,6 @@ __device__ __forceinline__ void nh_tile(const Buffers &b, const Params &p, int t
     const EventDesc ev = b.events[tl.event];
     const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
     tile_windows<U>(b, tl, ev, p.rwin_nh, sh);
-    if (sh.tsum >= (unsigned long long)DENSE_MEAN * tl.len) {
-        // warp form: lanes stride over one hit's window
-        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        for (int k = warp; k < tl.len; k += nwarps) {
-            const int q = tl.start + k;
-            const float4 me = nh_record(b, p, q);  // x, y, rho, id
-            const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * nbxy;
-            const Window w = window_of(me.x, me.y, p.rwin_nh, ev);
-            unsigned long long best = nh_none(p);
-            for (int by = w.ly; by <= w.hy; ++by) {
-                const int64_t row = plane + (int64_t)by * ev.nbx;
-                const int e = b.cell_start[row + w.hx + 1];
-                for (int u = b.cell_start[row + w.lx] + lane_id(); u < e; u += 32) {
-                    const float4 h = nh_record(b, p, u);
-                    const float d2 = sq_dist(me.x, me.y, h.x, h.y);
-                    const unsigned long long key = nh_key(d2, id_of(h));
-                    best = (h.z > me.z && key < best) ? key : best;
-                }
-            }
-            best = warp_min_u64(best);
-            if (lane_id() == 0) nh_store(b, p, q, id_of(me), me.z, best);
-        }
-        __syncthreads();
-        return;
-    }
     if (!tile_sorted(sh, p.band_cap)) {  // per-hit form
         for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
             const int q = tl.start + k;
@@ -401,9 +322,9 @@ __device__ __forceinline__ void nh_tile(const Buffers &b, const Params &p, int t
 // computed again by every tile whose band holds it (identical values); the
 // band restaged in place as (x, y, rho, id); nh and the decision of the
 // tile's hits.  So rho goes straight to nh with no pass over the batch in
-// between.  A tile the sorted form does not take (dense windows, a band
-// beyond the staging capacity, windows of more rows) or whose halo holds more
-// hits than the tile itself (dense neighbourhoods) gets only its rho here
+// between.  A tile the sorted form does not take (a band beyond the staging
+// capacity, windows of more rows) or whose halo holds more hits than the tile
+// itself (dense neighbourhoods) gets only its rho here
 // (rho_tile's forms) and joins a list that k_nh_rest finishes after every
 // tile's rho is written.
 template <int CHI, int U>
@@ -413,10 +334,9 @@ __device__ __forceinline__ void density_tile(const Buffers &b, const Params &p, 
     const EventDesc ev = b.events[tl.event];
     const FixedW fw = fixed_weights(b.wexp + 2 * tl.event, CHI);  // uniform per event
     tile_windows<U>(b, tl, ev, fmaxf(p.rwin_rho, p.rwin_nh), sh);
-    // fused when the windows are not dense, the band fits and its halo (whose
-    // rho is computed again here) holds at most as many hits as the tile
-    const bool fused = sh.tsum < (unsigned long long)DENSE_MEAN * tl.len &&
-                       tile_sorted(sh, p.band_cap) && sh.hi - sh.lo <= 2 * tl.len;
+    // fused when the band fits and its halo (whose rho is computed again here)
+    // holds at most as many hits as the tile
+    const bool fused = tile_sorted(sh, p.band_cap) && sh.hi - sh.lo <= 2 * tl.len;
     if (!fused) {
         __syncthreads();  // every thread has read the shared state rho_tile resets
         rho_tile<CHI, U>(b, p, t, sh, band);
