@@ -6,8 +6,9 @@
 // arrays into the region being filled, on that region's copy stream (so the
 // copies of different regions can use different copy engines); a launched region is
 // one clue_run_batch on the compute stream (after the region's copies), then
-// each event's results are copied into the caller's host output arrays, the
-// batch's device error word is read back, and a host callback on the stream
+// the batch's device error word is read back and cleared there, and on an
+// output stream (so the next batch need not wait for them) each event's
+// results are copied into the caller's output arrays and a host callback
 // (cudaLaunchHostFunc: no CUDA call inside, it only takes the scheduler's
 // lock) reports the batch done.  Nothing polls: the scheduler's worker sleeps
 // until a submission or such a callback wakes it.
@@ -40,6 +41,7 @@ class CudaBackend : public clue_serve::Backend {
         uint8_t *seed = nullptr;
         cudaStream_t copy = nullptr;  // the region's input copies (regions overlap theirs)
         cudaEvent_t staged = nullptr;
+        cudaEvent_t computed = nullptr;  // the batch's kernels and error readback are done
     };
 
     int device = 0;
@@ -48,6 +50,8 @@ class CudaBackend : public clue_serve::Backend {
     float prm[4] = {};
     clue_ctx *ctx = nullptr;
     cudaStream_t compute = nullptr;
+    cudaStream_t out = nullptr;  // result copies and completion callbacks (off the compute
+                                 // stream, so the next batch starts at once)
     std::vector<Region> regs;
     std::vector<Callback> cbs;     // one per region: a region runs one batch at a time
     unsigned *err_host = nullptr;  // pinned, one word per region
@@ -78,23 +82,27 @@ class CudaBackend : public clue_serve::Backend {
                                       (int32_t)reqs.size(), prm[0], prm[1], prm[2], prm[3],
                                       g.cid, g.seed);
         if (rc != CLUE_OK) return rc;
+        // the batch's own device errors: read the sticky word back and clear it
+        // before the next batch's kernels, on the compute stream
+        unsigned *err = clue::ctx_error_word(ctx);
+        if (cudaMemcpyAsync(&err_host[region], err, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                            compute) != cudaSuccess ||
+            cudaMemsetAsync(err, 0, sizeof(unsigned), compute) != cudaSuccess ||
+            cudaEventRecord(g.computed, compute) != cudaSuccess ||
+            cudaStreamWaitEvent(out, g.computed, 0) != cudaSuccess)
+            return CLUE_ERR_CUDA;
+        // each event's results into its own arrays, while the next batch runs
         for (size_t k = 0; k < reqs.size(); ++k) {
             const int64_t a = offs[k], n = offs[k + 1] - a;
             if (n == 0) continue;
             if (cudaMemcpyAsync(reqs[k].out[0], g.cid + a, (size_t)n * 4, cudaMemcpyDefault,
-                                compute) != cudaSuccess ||
+                                out) != cudaSuccess ||
                 cudaMemcpyAsync(reqs[k].out[1], g.seed + a, (size_t)n, cudaMemcpyDefault,
-                                compute) != cudaSuccess)
+                                out) != cudaSuccess)
                 return CLUE_ERR_CUDA;
         }
-        // the batch's own device errors: read the sticky word back and clear it
-        unsigned *err = clue::ctx_error_word(ctx);
-        if (cudaMemcpyAsync(&err_host[region], err, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                            compute) != cudaSuccess ||
-            cudaMemsetAsync(err, 0, sizeof(unsigned), compute) != cudaSuccess)
-            return CLUE_ERR_CUDA;
         cbs[region] = Callback{this, region, batch};
-        if (cudaLaunchHostFunc(compute, &CudaBackend::done, &cbs[region]) != cudaSuccess)
+        if (cudaLaunchHostFunc(out, &CudaBackend::done, &cbs[region]) != cudaSuccess)
             return CLUE_ERR_CUDA;
         return CLUE_OK;
     }
@@ -112,10 +120,12 @@ class CudaBackend : public clue_serve::Backend {
     void release() {
         cudaSetDevice(device);
         if (compute) cudaStreamSynchronize(compute);
+        if (out) cudaStreamSynchronize(out);
         for (Region &g : regs) {
             if (g.copy) cudaStreamSynchronize(g.copy);
             if (g.x) cudaFree(g.x);
             if (g.staged) cudaEventDestroy(g.staged);
+            if (g.computed) cudaEventDestroy(g.computed);
             if (g.copy) cudaStreamDestroy(g.copy);
         }
         regs.clear();
@@ -124,7 +134,8 @@ class CudaBackend : public clue_serve::Backend {
         if (err_host) cudaFreeHost(err_host);
         err_host = nullptr;
         if (compute) cudaStreamDestroy(compute);
-        compute = nullptr;
+        if (out) cudaStreamDestroy(out);
+        compute = out = nullptr;
     }
 };
 
@@ -172,7 +183,8 @@ int clue_server_create(clue_server **out, const clue_opts *opts, const clue_serv
         return rc;
     };
     if (cudaSetDevice(be.device) != cudaSuccess) return fail(CLUE_ERR_CUDA);
-    if (cudaStreamCreateWithFlags(&be.compute, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&be.compute, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&be.out, cudaStreamNonBlocking) != cudaSuccess)
         return fail(CLUE_ERR_CUDA);
     clue_opts o = *opts;
     o.stream = be.compute;
@@ -198,6 +210,7 @@ int clue_server_create(clue_server **out, const clue_opts *opts, const clue_serv
         g.cid = (int32_t *)(p + 4 * a4);
         g.seed = (uint8_t *)(p + 5 * a4);
         if (cudaEventCreateWithFlags(&g.staged, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.computed, cudaEventDisableTiming) != cudaSuccess ||
             cudaStreamCreateWithFlags(&g.copy, cudaStreamNonBlocking) != cudaSuccess)
             return fail(CLUE_ERR_CUDA);
     }
