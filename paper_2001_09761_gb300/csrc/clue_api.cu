@@ -370,40 +370,48 @@ int upload_tables_async(clue_ctx *ctx, const Plan &plan) {
 // The density kernels' staging capacity for a run: a tile's band holds its
 // own hits and about a window's height of grid rows around them, so the
 // expected band of an event is its tile length plus (window rows) x (hits per
-// grid row, from the event's mean over max_layers layers), with a quarter in
-// reserve; the largest over the run's events, within [BAND_CAP_MIN,
-// BAND_CAP_MAX].  Tiles whose band is larger take the per-hit or warp forms.
-int band_cap_for(const clue_ctx *ctx, const Plan &plan, const Params &p) {
+// grid row, from the event's mean over max_layers layers).  The capacity is
+// the largest over the run's events with a quarter in reserve, within
+// [BAND_CAP_MIN, BAND_CAP_MAX] (tiles whose band is larger take the per-hit
+// form); *mean_band is the hit-weighted mean of the expected bands.
+int band_cap_for(const clue_ctx *ctx, const Plan &plan, const Params &p, double *mean_band) {
     const double r = std::max(p.rwin_rho, p.rwin_nh);
-    double most = 0.0;
+    double most = 0.0, sum = 0.0, hits = 0.0;
     for (const EventDesc &d : plan.ev) {
         if (d.n <= 0) continue;
         const double s = 1.0 / d.inv_s;
         const double rows = std::ceil(2.0 * r / s) + 1.0;
         const double per_row = (double)d.n / ((double)ctx->opts.max_layers * d.nby);
         const double tlen = std::min<double>(d.n, ctx->tile_len[class_of(d.n)]);
-        most = std::max(most, 1.25 * (tlen + rows * per_row));
+        const double band = tlen + rows * per_row;
+        most = std::max(most, 1.25 * band);
+        sum += band * d.n;
+        hits += d.n;
     }
+    *mean_band = hits > 0.0 ? sum / hits : 0.0;
     const int cap = ctx->band_cap > 0 ? ctx->band_cap : (int)std::ceil(most / 256.0) * 256;
     return std::min(BAND_CAP_MAX, std::max(BAND_CAP_MIN, cap));
 }
 
+// Shared memory of one density CTA: the per-tile state and the staged band.
+int density_smem(int band_cap) { return DENSITY_SMEM_FIXED + band_cap * 16; }
+
 // The density kernels run one CTA per tile.  Unless the options or the
 // tuning table fix their block size, a run with at least a tile per SM uses
-// 256 threads (four CTAs per SM, as their shared memory allows with the
-// smallest staging capacity; two CTAs of 512 threads when the staging is
-// larger), a smaller one 1024 (one hit per thread: its few tiles' hits all in
-// flight at once).
+// 256 threads (four CTAs per SM while their shared memory lets four share
+// an SM, 57 KB each; else CTAs of 512 threads, two per SM), a smaller one
+// 1024 (one hit per thread: its few tiles' hits all in flight at once).
 LaunchCfg make_cfg(const clue_ctx *ctx, int64_t ntiles, int band_cap) {
     LaunchCfg c;
     c.block_fill = 256;
-    const int automatic = ntiles < ctx->num_sms ? 1024 : band_cap > BAND_CAP_MIN ? 512 : 256;
+    const bool wide = density_smem(band_cap) > 57 * 1024;
+    const int automatic = ntiles < ctx->num_sms ? 1024 : wide ? 512 : 256;
     c.block_density = ctx->opts.block_size > 0 ? ctx->opts.block_size
                     : ctx->block_density > 0   ? ctx->block_density
                                                : automatic;
     // a tuned block below 512 threads would leave a run with wide staging (two
     // CTAs per SM) at half occupancy: such runs keep at least 512
-    if (ctx->opts.block_size == 0 && band_cap > BAND_CAP_MIN && ntiles >= ctx->num_sms)
+    if (ctx->opts.block_size == 0 && wide && ntiles >= ctx->num_sms)
         c.block_density = std::max(c.block_density, 512);
     c.grid_cap = ctx->num_sms * 8;
     return c;
@@ -656,11 +664,13 @@ int run_batch(clue_ctx *ctx, const float *x, const float *y, const int32_t *laye
     b.is_seed = is_seed;
     b.ctrl = ctx->d_ctrl;
     Params p = make_params(ctx, dc, rhoc, delta_c, delta_o);
-    p.band_cap = band_cap_for(ctx, plan, p);
-    // the fused density kernel where the run's bands fit the smallest staging
-    // (its halo recomputation is cheap there), else the separate kernels
+    double mean_band = 0.0;
+    p.band_cap = band_cap_for(ctx, plan, p, &mean_band);
+    // the fused density kernel where the run's bands, on the hit-weighted mean,
+    // fit the smallest staging (sparse grid rows: its halo recomputation is
+    // cheap there), else the separate kernels
     p.fused = ctx->opts.density == CLUE_DENSITY_FUSED ||
-              (ctx->opts.density == CLUE_DENSITY_AUTO && p.band_cap == BAND_CAP_MIN);
+              (ctx->opts.density == CLUE_DENSITY_AUTO && mean_band <= BAND_CAP_MIN);
     b.rho_in_spr = p.fused ? 0 : 1;
     const LaunchCfg cfg = make_cfg(ctx, (int64_t)plan.tiles.size(), p.band_cap);
 

@@ -22,6 +22,8 @@ constexpr int SEG_MAX_CELLS = 16384;
 // shared memory within the default 48 KB.
 constexpr int BAND_CAP_MIN = 1792;
 constexpr int BAND_CAP_MAX = 6144;
+// Static shared memory of a density CTA (its per-tile state), besides the band.
+constexpr int DENSITY_SMEM_FIXED = 18720;
 
 // Cluster id of a follower whose id has not been passed down yet (frontier
 // expansion).

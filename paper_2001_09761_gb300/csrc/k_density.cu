@@ -6,6 +6,8 @@
 
 namespace clue {
 
+static_assert(sizeof(DensityShared) <= DENSITY_SMEM_FIXED, "the host's occupancy estimate");
+
 size_t band_bytes(const Params &p) { return (size_t)p.band_cap * sizeof(float4); }
 
 // Each density kernel in two builds: CTAs of up to 256 threads (the usual
