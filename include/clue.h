@@ -287,7 +287,7 @@ int64_t clue_scratch_bytes(clue_ctx *ctx);
  * block or fail, or a plugin whose host owns every device allocation.  It runs
  * the same kernels as clue_run, so results are bit-identical to clue_run's,
  * but every scratch array lives in one fixed array in the library's device
- * memory (about 14.2 MB, held on every GPU that loads the library until the
+ * memory (about 14.7 MB, held on every GPU that loads the library until the
  * process exits).  It needs no context and calls no allocator, neither CUDA's
  * nor any other.
  *

@@ -22,7 +22,8 @@ LIB = PKG / "libclue.so"
 SOURCES = ["clue_api.cu", "k_grid.cu", "k_density.cu", "k_assign.cu", "clue_static.cu",
            "clue_serve.cu", "serve_core.cpp"]
 HEADERS = ["clue_internal.h", "device_common.cuh", "scan.cuh", "grid_stages.cuh",
-           "density_stages.cuh", "density_tile.cuh", "assign_stages.cuh", "serve_core.h"]
+           "density_stages.cuh", "density_tile.cuh", "bulk_copy.cuh", "assign_stages.cuh",
+           "serve_core.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

@@ -11,8 +11,6 @@ namespace clue {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
-// Squared distance in fp32, every operation rounded on its own (no FMA):
-// dx = xj - xi, dy = yj - yi, dx*dx + dy*dy.  It is exactly symmetric in i, j.
 // An event's weight range: [0] the min of max(biased exponent, 1), [1] the
 // min of 255 - biased exponent, over its finite nonzero weights (all ones:
 // none yet).  A CTA gathers its tile's range in shared memory: a warp-wide
@@ -81,6 +79,8 @@ __device__ __forceinline__ long long fixed_weight_of(const float4 &h) {
     return (long long)(((unsigned long long)__float_as_uint(h.w) << 32) | __float_as_uint(h.z));
 }
 
+// Squared distance in fp32, every operation rounded on its own (no FMA):
+// dx = xj - xi, dy = yj - yi, dx*dx + dy*dy.  It is exactly symmetric in i, j.
 __device__ __forceinline__ float sq_dist(float xi, float yi, float xj, float yj) {
     const float dx = __fsub_rn(xj, xi);
     const float dy = __fsub_rn(yj, yi);

@@ -22,8 +22,10 @@ template <int CHI, int MAXT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 1) k_rho(Buffers b, Params p) {
     __shared__ DensityShared sh;
     extern __shared__ float4 band[];  // Params::band_cap records
+    stage_init(sh);
+    unsigned parity = 0u;
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x)
-        rho_tile<CHI, DT_ILP>(b, p, t, sh, band);
+        if (!rho_tile<CHI, DT_ILP>(b, p, t, sh, band, parity)) return;
 }
 
 template <int CHI>
@@ -52,8 +54,10 @@ template <int MAXT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 1) k_nh(Buffers b, Params p) {
     __shared__ DensityShared sh;
     extern __shared__ float4 band[];  // Params::band_cap records
+    stage_init(sh);
+    unsigned parity = 0u;
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x)
-        nh_tile<DT_ILP>(b, p, t, sh, band);
+        if (!nh_tile<DT_ILP>(b, p, t, sh, band, parity)) return;
 }
 
 cudaError_t launch_nh(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
@@ -72,8 +76,10 @@ template <int CHI, int MAXT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 1) k_density(Buffers b, Params p) {
     __shared__ DensityShared sh;
     extern __shared__ float4 band[];  // Params::band_cap records
+    stage_init(sh);
+    unsigned parity = 0u;
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x)
-        density_tile<CHI, DT_ILP>(b, p, t, sh, band);
+        if (!density_tile<CHI, DT_ILP>(b, p, t, sh, band, parity)) return;
 }
 
 template <int CHI>
@@ -100,8 +106,11 @@ template <int MAXT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 1) k_nh_rest(Buffers b, Params p) {
     __shared__ DensityShared sh;
     extern __shared__ float4 band[];  // Params::band_cap records
+    stage_init(sh);
+    unsigned parity = 0u;
     const int n = b.ctrl->nrest;
-    for (int i = blockIdx.x; i < n; i += gridDim.x) nh_tile<DT_ILP>(b, p, b.rest[i], sh, band);
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+        if (!nh_tile<DT_ILP>(b, p, b.rest[i], sh, band, parity)) return;
 }
 
 cudaError_t launch_nh_rest(const Buffers &b, const Params &p, const LaunchCfg &c,
