@@ -182,7 +182,8 @@ ALG_BYTES = {
     "density": 16 + 4 + 4 + 4 + 4 + 8,  # x, y, w, layer, id in; rho, code, (delta^2, nh) out
     "nh_rest": 0,                      # nothing unless a tile is dense or its band too long
     "link": 4 + 4 + 4 + 1,             # code, seed rank in; id, seed flag out
-    "assign": 4 + 4 + 4 + 1,           # code, the nh's code, seed bits in; id, seed flag out
+    "seed_codes": 0,                   # seed bits and word ranks in (N/8 B), seeds' codes out
+    "assign": 4 + 4 + 1,               # code, the nh's code in; id, seed flag out
     "expand_level": 8 + 4 + 4 + 4,     # list range, parent id, follower in; id out
     "complete": 4 + 4,                 # id in, id out
     "jump": 0,                         # nothing unless a chain outruns the bounded walk
@@ -199,7 +200,7 @@ STAGED_BYTES = {"S1": 16, "S2": 16, "S3": 24, "S4": 21, "S5": 8}
 STEP_OF_KERNEL = {"fill_layers": "S1", "fill_place": "S1", "fill_cells": "S1",
                   "fill_count": "S1", "fill_scatter": "S1", "fill_canon": "S1",
                   "rho": "S2", "nh_delta": "S3", "density": "S2+S3", "nh_rest": "S3",
-                  "scan_hits": "S4", "link": "S4", "assign": "S4+S5",
+                  "scan_hits": "S4", "link": "S4", "seed_codes": "S4", "assign": "S4+S5",
                   "expand_level": "S5", "complete": "S5", "jump": "S5"}
 COMPULSORY_BYTES = 21
 STAGED_TOTAL = sum(STAGED_BYTES.values())

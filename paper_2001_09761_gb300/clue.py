@@ -214,7 +214,8 @@ STAGE_OF = {"fill_layers": "grid_fill", "scan_segs": "grid_fill", "fill_place": 
             "fill_count": "grid_fill", "scan_cells": "grid_fill", "fill_scatter": "grid_fill",
             "fill_canon": "grid_fill", "rho": "density", "nh_delta": "density",
             "density": "density", "nh_rest": "density",
-            "scan_hits": "decide_followers", "link": "decide_followers", "assign": "expand",
+            "scan_hits": "decide_followers", "link": "decide_followers",
+            "seed_codes": "decide_followers", "assign": "expand",
             "expand_level": "expand", "complete": "expand", "jump": "expand"}
 
 
@@ -294,6 +295,10 @@ class Clusterer:
         self.max_layers = max_layers
         self.ctx = clue_create(o)
         self._last_n = 0
+        # reused events that order the clusterer's stream after the caller's
+        # current stream and back (one record and one wait each way per call)
+        self._ev_in = torch.cuda.Event()
+        self._ev_out = torch.cuda.Event()
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -307,16 +312,22 @@ class Clusterer:
             pass
 
     def _begin(self, tensors):
-        t = self.torch
-        self.stream.wait_stream(t.cuda.current_stream(self.device))
+        cur = self.torch.cuda.current_stream(self.device)
+        self._ev_in.record(cur)
+        self.stream.wait_event(self._ev_in)
         for x in tensors:
             x.record_stream(self.stream)
+        self._cur = cur
 
     def _end(self):
-        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        self._ev_out.record(self.stream)
+        self._cur.wait_event(self._ev_out)
 
     def _as(self, a, dtype):
         t = self.torch
+        if isinstance(a, t.Tensor) and a.dtype == dtype and a.device == self.device and \
+                a.is_contiguous():
+            return a
         if isinstance(a, np.ndarray):
             a = t.from_numpy(np.ascontiguousarray(a))
         a = a.to(device=self.device, dtype=dtype)
@@ -368,7 +379,8 @@ class Clusterer:
         offsets = np.ascontiguousarray(offsets, np.int64)
         n = x.shape[0]
         cid, seed = out if out is not None else (np.empty(n, np.int32), np.empty(n, np.uint8))
-        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        self._ev_in.record(self.torch.cuda.current_stream(self.device))
+        self.stream.wait_event(self._ev_in)
         ptr = lambda a: a.ctypes.data
         rc = clue_run_batch_host(self.ctx, ptr(x), ptr(y), ptr(layer), ptr(energy), offsets,
                                  len(offsets) - 1, *[float(v) for v in params], ptr(cid),

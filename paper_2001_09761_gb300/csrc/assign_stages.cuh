@@ -144,8 +144,8 @@ __device__ __forceinline__ void jump_rounds(const Buffers &b, int np, int rounds
 // Chase mode (CLUE_EXPAND_CHASE): ids with no follower lists.  Every hit walks
 // its chain of codes (a follower's code is its nearest-higher) up to the first
 // hit that is not a follower, and takes that hit's id: a seed's rank among its
-// event's seeds (from the seed bits), or -1 at an outlier or at a hit with no
-// nearest-higher -- the closed form "a follower inherits the id of its
+// event's seeds (k_seed_codes has put the seed's rank among the batch's seeds
+// in its code), or -1 at an outlier or at a hit with no nearest-higher -- the closed form "a follower inherits the id of its
 // nearest-higher" of Algorithm 3's expansion.  A seed's chain is the seed
 // itself.  Chains are finite because rho rises strictly along them.  The walk
 // takes at most min(CHASE_STEPS, walk limit) steps; a hit whose chain is
@@ -176,7 +176,7 @@ __device__ __forceinline__ void assign_stage(const Buffers &b, const Params &p) 
                 c[u] = cn[u];
                 const int kn = k + U * (int)blockDim.x;
                 cn[u] = kn < tl.len ? b.code[tl.start + kn] : CODE_NOISE;
-                if (act[u]) b.is_seed[v[u]] = c[u] == CODE_SEED;
+                if (act[u]) b.is_seed[v[u]] = c[u] <= CODE_SEED;
             }
             bool any = true;
             for (int steps = 0; any && steps < kmax; ++steps) {
@@ -195,7 +195,7 @@ __device__ __forceinline__ void assign_stage(const Buffers &b, const Params &p) 
                 const int g = tl.start + k0 + u * (int)blockDim.x;
                 const bool pend = act[u] && c[u] >= 0;  // chain longer than the walk
                 int id = -1;
-                if (c[u] == CODE_SEED) id = seed_rank(b, v[u]) - ebase;
+                if (c[u] <= CODE_SEED) id = (CODE_SEED - c[u]) - ebase;  // the seed's rank
                 if (pend) id = PENDING;
                 if (act[u]) b.cid[g] = id;
                 pend_hit(b, mask, pend, g, c[u]);

@@ -484,11 +484,13 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(launch_scan_hits(b, p, cfg, s, &nl));
     CK(rec("scan_hits"));
     if (p.chase) {
+        CK(launch_seed_codes(b, cfg, s));
+        CK(rec("seed_codes"));
         CK(launch_assign(b, p, cfg, s));
         CK(rec("assign"));
         CK(launch_jump(b, p, s));
         CK(rec("jump"));
-        nl += 4;  // rho, nh (with the decision), assign, jump
+        nl += 5;  // rho, nh (with the decision), seed codes, assign, jump
     } else {
         CK(launch_link(b, p, cfg, s));
         CK(rec("link"));

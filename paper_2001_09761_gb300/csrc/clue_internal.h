@@ -31,7 +31,10 @@ constexpr int32_t PENDING = -2;
 
 // Outcome of the decision step per hit (Sec. 2.2): a follower stores its
 // nearest-higher (>= 0); otherwise one of these codes.
-constexpr int32_t CODE_NOISE = -1, CODE_SEED = -2, CODE_OUTLIER = -3;
+constexpr int32_t CODE_NOISE = -1, CODE_OUTLIER = -2, CODE_SEED = -3;
+// In chase mode, once the seed ranks are known, seed g's code becomes
+// CODE_SEED - R, R its rank among the batch's seeds (R <= 2^31 - 3, so the
+// code stays at or above INT32_MIN): the codes <= CODE_SEED are the seeds.
 
 // Error bits raised on the device (ctrl->err).
 constexpr unsigned ERRBIT_INPUT = 1u, ERRBIT_TIMEOUT = 2u;
@@ -204,6 +207,7 @@ cudaError_t launch_nh_rest(const Buffers &b, const Params &p, const LaunchCfg &c
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s,
                              int *launches);
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_seed_codes(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_assign(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);  // all levels
 cudaError_t launch_expand_level(const Buffers &b, const LaunchCfg &c, int level, cudaStream_t s);

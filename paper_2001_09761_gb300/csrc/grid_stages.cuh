@@ -214,6 +214,62 @@ __device__ __forceinline__ void smem_zero4(int *a, int n4) {
     for (int c = threadIdx.x; c < n4; c += blockDim.x) a4[c] = make_int4(0, 0, 0, 0);
 }
 
+// Exclusive scan, in place, of 16-bit counts packed two to a word (cell 2w in
+// the low half of word w, 2w + 1 in the high half), a[0..4 * n4) words in
+// shared memory (16-byte aligned), by the whole CTA, as smem_excl_scan4 does
+// for ints; every prefix must stay below 2^16.  Ends with a barrier.
+__device__ __forceinline__ void smem_excl_scan16(unsigned *a, int n4, int *ws) {
+    uint4 *a4 = reinterpret_cast<uint4 *>(a);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (((n4 + nw - 1) / nw) + 31) & ~31;
+    const int c0 = min(warp * per, n4), c1 = min(c0 + per, n4);
+    // the sum of a word's two halves, and of a uint4's eight
+    auto hsum = [](unsigned w) { return (int)((w & 0xffffu) + (w >> 16)); };
+    int sum = 0;
+    for (int c = c0 + lane; c < c1; c += 32) {
+        const uint4 v = a4[c];
+        sum += (hsum(v.x) + hsum(v.y)) + (hsum(v.z) + hsum(v.w));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL_MASK, sum, o);
+    if (lane == 0) ws[warp] = sum;
+    __syncthreads();
+    if (warp == 0) {
+        const int v = lane < nw ? ws[lane] : 0;
+        const int incl = warp_incl_scan(v);
+        if (lane < nw) ws[lane] = incl - v;
+    }
+    __syncthreads();
+    int run = ws[warp];
+    for (int base = c0; base < c1; base += 32) {
+        const int c = base + lane;
+        const uint4 v = c < c1 ? a4[c] : make_uint4(0u, 0u, 0u, 0u);
+        const int t = (hsum(v.x) + hsum(v.y)) + (hsum(v.z) + hsum(v.w));
+        const int incl = warp_incl_scan(t);
+        unsigned e = (unsigned)(run + incl - t);  // exclusive offset of the uint4's first cell
+        unsigned o[4];
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const unsigned lo = e, hi = e + (w[i] & 0xffffu);
+            o[i] = lo | (hi << 16);
+            e = hi + (w[i] >> 16);
+        }
+        if (c < c1) a4[c] = make_uint4(o[0], o[1], o[2], o[3]);
+        run += __shfl_sync(FULL_MASK, incl, 31);
+    }
+    __syncthreads();
+}
+
+// A 16-bit counter of the packed array: add one, return its old value.
+__device__ __forceinline__ int inc16(unsigned *a, unsigned c) {
+    const unsigned sh = (c & 1u) << 4;
+    return (int)((atomicAdd(&a[c >> 1], 1u << sh) >> sh) & 0xffffu);
+}
+__device__ __forceinline__ int get16(const unsigned *a, unsigned c) {
+    return (int)((a[c >> 1] >> ((c & 1u) << 4)) & 0xffffu);
+}
+
 __device__ __forceinline__ int cell_in_layer(float x, float y, const EventDesc &ev) {
     return axis_bin(y, ev.ymin, ev.inv_s, ev.nby) * ev.nbx + axis_bin(x, ev.xmin, ev.inv_s, ev.nbx);
 }
@@ -238,6 +294,11 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
         const Tile tl = b.tiles[t];
         smem_zero4(s_off, L4);
         if (threadIdx.x == 0) s_w[0] = s_w[1] = 0xffffffffu;
+        // the tile's run start in the segment of layer threadIdx.x, loaded now
+        // and used after the ranking (no round trip of its own; layers past
+        // the block size load theirs then)
+        const EventDesc ev = b.events[tl.event];
+        const int tb0 = (int)threadIdx.x < p.L ? b.tbase[run_index(ev, p.L, threadIdx.x, t)] : 0;
         float4 r[PER];
         int lay[PER];
 #pragma unroll
@@ -276,7 +337,10 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
         }
         __syncthreads();
         smem_excl_scan4(s_off, L4, ws);
-        if (threadIdx.x == 0) weight_range_flush(b.wexp + 2 * tl.event, s_w);
+        if (threadIdx.x == 0) {  // no read first: the thread does not wait on the atomics
+            if (s_w[0] != 0xffffffffu) atomicMin(&b.wexp[2 * tl.event], s_w[0]);
+            if (s_w[1] != 0xffffffffu) atomicMin(&b.wexp[2 * tl.event + 1], s_w[1]);
+        }
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int k = threadIdx.x + u * FILL_THREADS;
@@ -287,12 +351,13 @@ __device__ __forceinline__ void fill_place_stage(const Buffers &b, const Params 
             }
         }
         __syncthreads();
-        // slot i of layer l goes to dst[l] + i (only the tile's layers are read)
-        const EventDesc ev = b.events[tl.event];
+        // slot i of layer l goes to dst[l] + i (only the tile's layers are set)
         int *s_dst = s_off + 4 * L4;
         for (int l = threadIdx.x; l < p.L; l += FILL_THREADS) {
             const int end = l + 1 < p.L ? s_off[l + 1] : tl.len;
-            if (end > s_off[l]) s_dst[l] = b.tbase[run_index(ev, p.L, l, t)] - s_off[l];
+            if (end > s_off[l])
+                s_dst[l] = (l == (int)threadIdx.x ? tb0 : b.tbase[run_index(ev, p.L, l, t)]) -
+                           s_off[l];
         }
         __syncthreads();
         for (int i = threadIdx.x; i < tl.len; i += FILL_THREADS) {
@@ -315,34 +380,43 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) 
 // prefetched into L2 (they are read once more, in sorted order, at the end).
 // Its hits are counted per cell in shared memory (cells from `cell16`), the
 // counts scanned and the layer's cell offsets written.  A segment of at most
-// SEG_SMEM_HITS hits is then permuted in shared memory: a second pass over
-// its cells (just read, so in L2) takes each hit's slot with a shared atomic
-// on its cell's running offset and stores the hit's 16-bit index there; the
+// SEG_SMEM_HITS hits keeps 16-bit counters, two to a word (its offsets stay
+// below 2^16), and is then permuted in shared memory: a second pass over its
+// cells (just read, so in L2) takes each hit's slot with a shared atomic on
+// its cell's running offset and stores the hit's 16-bit index there; the
 // records are then written in slot order, a gather from L2 and coalesced
-// stores.  A longer segment keeps the first pass's ranks in `perm` and writes
-// each record at its cell's offset plus its rank.  Loads are issued in
-// batches ahead of the atomics and stores that use them; the kernel keeps to
-// 42 registers so that three CTAs share an SM.  The last segment also writes
-// the end offset cell_start[C].  Needs SEG_THREADS threads, and nbx * nby ints
-// (rounded up to a multiple of 4) plus SEG_SMEM_HITS 16-bit indices of dynamic
-// shared memory.
+// stores.  A longer segment counts in 32-bit words, keeps the first pass's
+// ranks in `perm` and writes each record at its cell's offset plus its rank.
+// Loads are issued in batches ahead of the atomics and stores that use them;
+// the kernel keeps to 42 registers so that three CTAs share an SM (the
+// shared memory of a 16k-cell layer allows three).  The last segment also
+// writes the end offset cell_start[C].  Needs SEG_THREADS threads and
+// fill_cells_smem(nbx * nby) bytes of dynamic shared memory.
+__host__ __device__ constexpr int fill_cells_smem(int max_cells) {
+    return (max_cells + 3) / 4 * 16 > (max_cells + 7) / 8 * 16 + SEG_SMEM_HITS * 2
+               ? (max_cells + 3) / 4 * 16
+               : (max_cells + 7) / 8 * 16 + SEG_SMEM_HITS * 2;
+}
+
 __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params &p) {
     extern __shared__ int4 s_cell4[];
     __shared__ int ws[32];
-    int *s_cell = reinterpret_cast<int *>(s_cell4);
-    unsigned short *s_perm = (unsigned short *)(s_cell4 + (b.max_cells + 3) / 4);
+    int *s_cell = reinterpret_cast<int *>(s_cell4);             // 32-bit counters (long segments)
+    unsigned *s_c16 = reinterpret_cast<unsigned *>(s_cell4);    // 16-bit counters (short ones)
+    unsigned short *s_perm = (unsigned short *)(s_cell4 + (b.max_cells + 7) / 8);
     constexpr int C = 8;  // cells loaded per batch
     constexpr int G = 2;  // gathers in flight per thread
     for (int64_t sg = blockIdx.x; sg < b.nseg; sg += gridDim.x) {
         const int e = (int)(sg / p.L);
         const int l = (int)(sg - (int64_t)e * p.L);
         const EventDesc ev = b.events[e];
-        const int nbxy = ev.nbx * ev.nby, n4 = (nbxy + 3) / 4;
+        const int nbxy = ev.nbx * ev.nby;
         const int64_t cbase = ev.cell_off + (int64_t)l * nbxy;
         // the segment runs from its first tile's run to the next segment's
         const int s0 = b.tbase[run_index(ev, p.L, l, ev.tile0)];
         const int n = b.tbase[run_index(ev, p.L, l + 1, ev.tile0)] - s0;
         const bool small = n <= SEG_SMEM_HITS;  // uniform over the CTA
+        const int n4 = small ? (nbxy + 7) / 8 : (nbxy + 3) / 4;
         const FixedW fw = fixed_weights(b.wexp + 2 * e, p.chi);
         if (small && n > 0 && threadIdx.x == 0) prefetch_l2_bulk(b.rec + s0, (unsigned)n * 16u);
         const unsigned short *cell = b.cell16 + s0;
@@ -358,13 +432,24 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
 #pragma unroll
             for (int u = 0; u < C; ++u) {
                 if (c[u] == 0xffffu) break;
-                const int rk = atomicAdd(&s_cell[c[u]], 1);
-                if (!small) b.perm[s0 + k0 + u * SEG_THREADS] = rk;
+                if (small) {
+                    inc16(s_c16, c[u]);
+                } else {
+                    const int rk = atomicAdd(&s_cell[c[u]], 1);
+                    b.perm[s0 + k0 + u * SEG_THREADS] = rk;
+                }
             }
         }
         __syncthreads();
-        smem_excl_scan4(s_cell, n4, ws);
-        for (int c = threadIdx.x; c < nbxy; c += SEG_THREADS) b.cell_start[cbase + c] = s0 + s_cell[c];
+        if (small) {
+            smem_excl_scan16(s_c16, n4, ws);
+            for (int c = threadIdx.x; c < nbxy; c += SEG_THREADS)
+                b.cell_start[cbase + c] = s0 + get16(s_c16, (unsigned)c);
+        } else {
+            smem_excl_scan4(s_cell, n4, ws);
+            for (int c = threadIdx.x; c < nbxy; c += SEG_THREADS)
+                b.cell_start[cbase + c] = s0 + s_cell[c];
+        }
         if (sg == b.nseg - 1 && threadIdx.x == 0) b.cell_start[b.C] = s0 + n;
         if (small) {
             __syncthreads();  // the offsets are read before they become cursors
@@ -378,7 +463,7 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
 #pragma unroll
                 for (int u = 0; u < C; ++u) {
                     if (c[u] == 0xffffu) break;
-                    s_perm[atomicAdd(&s_cell[c[u]], 1)] = (unsigned short)(k0 + u * SEG_THREADS);
+                    s_perm[inc16(s_c16, c[u])] = (unsigned short)(k0 + u * SEG_THREADS);
                 }
             }
             __syncthreads();

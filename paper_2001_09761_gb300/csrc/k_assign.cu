@@ -23,6 +23,39 @@ cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, c
     return cudaGetLastError();
 }
 
+// Chase mode, after the seed scan: every seed's code becomes CODE_SEED - R,
+// R its rank among the batch's seeds (word prefix + the set bits below it),
+// so that every chain's walk ends with its seed's rank in hand instead of
+// two more scattered loads (the rank's word and bits) per hit.  A warp loads
+// 32 words of the bitmap and their prefixes at once (coalesced), then takes
+// its non-empty words one at a time, a lane per bit (coalesced code stores).
+__global__ void __launch_bounds__(256) k_seed_codes(Buffers b) {
+    const int64_t nw = b.N / 32 + 1;  // the words the seed scan covers
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned below = lanemask_lt(), me = 1u << lane_id();
+    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < nw;
+         w0 += nwarps * 32) {
+        const int64_t wl = w0 + lane_id();
+        const unsigned mine = wl < nw ? b.sbits[wl] : 0u;
+        const int rmine = wl < nw ? b.sword[wl] : 0;
+        unsigned todo = __ballot_sync(FULL_MASK, mine != 0u);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const unsigned bits = __shfl_sync(FULL_MASK, mine, j);
+            const int r = __shfl_sync(FULL_MASK, rmine, j);
+            if (bits & me) b.code[(w0 + j) * 32 + lane_id()] = CODE_SEED - (r + __popc(bits & below));
+        }
+    }
+}
+
+cudaError_t launch_seed_codes(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {
+    const int64_t blocks = (b.N / 32 + 1 + 255) / 256;  // 32 words per warp
+    const int grid = (int)(blocks < c.grid_cap ? blocks : c.grid_cap);
+    k_seed_codes<<<grid > 0 ? grid : 1, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256, 2) k_assign(Buffers b, Params p) { assign_stage(b, p); }
 
 // One CTA per tile (chain lengths vary; see launch_rho).

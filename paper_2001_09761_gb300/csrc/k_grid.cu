@@ -67,7 +67,6 @@ __global__ void __launch_bounds__(SEG_THREADS, 3) k_fill_cells(Buffers b, Params
     fill_cells_stage(b, p);
 }
 
-constexpr int fill_cells_smem(int max_cells) { return (max_cells + 3) / 4 * 16 + SEG_SMEM_HITS * 2; }
 
 cudaError_t fill_prepare() {
     return cudaFuncSetAttribute(k_fill_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
