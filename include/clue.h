@@ -244,9 +244,12 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
 /* Write the tuning table as text into buf (capacity cap bytes,
  * NUL-terminated): a comment line, then per class "class <lo> <hi>
  * <bin_scale> <tile_hits>" (bin size = bin_scale * 2 d_c; tile_hits: hits
- * per CTA of the per-tile kernels, a multiple of 32 up to 1024), then
- * "block <threads>" (0 = by run size).  Returns the length needed, or a
- * negative CLUE_ERR_* code.  (No counterpart in the paper: tuning state.) */
+ * per CTA of the per-tile kernels, a multiple of 32 up to 1024) for the six
+ * classes (edges 0, 32768, 100000, 316228, 1000000, 3162278 hits), then
+ * "block <threads>" (0 = by run size) and "band <staged records>" (the
+ * density kernels' staging capacity, 0 = by run).  Returns the length
+ * needed, or a negative CLUE_ERR_* code.  (No counterpart in the paper:
+ * tuning state.) */
 int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap);
 
 /* Replace the tuning table from text in the format of clue_get_tuning (a

@@ -26,8 +26,9 @@ using namespace clue;
 
 namespace {
 
-constexpr int NCLASS = 5;
-constexpr int64_t CLASS_EDGE[NCLASS + 1] = {0, 32768, 100000, 316228, 1000000, INT64_MAX};
+constexpr int NCLASS = 6;  // event-size classes of the tuning table, half a decade apart
+constexpr int64_t CLASS_EDGE[NCLASS + 1] = {0, 32768, 100000, 316228, 1000000, 3162278,
+                                            INT64_MAX};
 constexpr int NPROF = 40;  // profiling events: one before the first kernel, one after each group
 constexpr int NPSETS = 4;  // profiled runs whose times stay readable (a ring of event sets)
 constexpr int NSTAGING = 4;
@@ -827,8 +828,9 @@ int clue_create(clue_ctx **out, const clue_opts *opts) {
     ctx->device = o.device;
     // Bin size in units of 2 d_c per event-size class: about one hit per cell
     // or fewer for events spread over many layers (what the autotuner picks
-    // on such events); the smaller the event, the sparser its layers.
-    const float defaults[NCLASS] = {8.0f, 4.0f, 3.0f, 2.0f, 1.0f};
+    // on such events); the smaller the event, the sparser its layers, the
+    // larger, the denser (a 5M-hit event of 50 layers picks 0.5).
+    const float defaults[NCLASS] = {12.0f, 4.0f, 2.0f, 2.0f, 1.0f, 0.5f};
     for (int k = 0; k < NCLASS; ++k) {
         ctx->bin_scale[k] = defaults[k];
         ctx->tile_len[k] = TILE;
@@ -1253,7 +1255,7 @@ int clue_autotune(clue_ctx *ctx, const float *x, const float *y, const int32_t *
 
 int64_t clue_get_tuning(clue_ctx *ctx, char *buf, int64_t cap) {
     if (!ctx) return -CLUE_ERR_ARG;
-    std::string s = "# clue tuning v2: class <lo> <hi> <bin_scale> <tile_hits>; block <threads>; "
+    std::string s = "# clue tuning v3: class <lo> <hi> <bin_scale> <tile_hits>; block <threads>; "
                     "band <staged records>\n";
     char line[160];
     for (int k = 0; k < NCLASS; ++k) {

@@ -692,7 +692,7 @@ def test_autotune_keeps_results(clue_mod):
                               oracle.run_event(ev, gen.PARAMS_BLOBS, 100)["cluster_id"])
     cl.tuning = table  # round-trips through the text format
     assert cl.tuning == table
-    assert len([ln for ln in table.splitlines() if ln.startswith("class")]) == 5
+    assert len([ln for ln in table.splitlines() if ln.startswith("class")]) == 6
     for ln in table.splitlines():
         if ln.startswith("class"):
             assert int(ln.split()[4]) in (256, 512, 1024)
