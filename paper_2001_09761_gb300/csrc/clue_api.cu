@@ -485,13 +485,16 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
     CK(launch_scan_hits(b, p, cfg, s, &nl));
     CK(rec("scan_hits"));
     if (p.chase) {
-        CK(launch_seed_codes(b, cfg, s));
-        CK(rec("seed_codes"));
+        if (seed_codes_separate(b)) {  // else the one-CTA seed scan wrote them
+            CK(launch_seed_codes(b, cfg, s));
+            CK(rec("seed_codes"));
+            ++nl;
+        }
         CK(launch_assign(b, p, cfg, s));
         CK(rec("assign"));
         CK(launch_jump(b, p, s));
         CK(rec("jump"));
-        nl += 5;  // rho, nh (with the decision), seed codes, assign, jump
+        nl += 4;  // rho, nh (with the decision), assign, jump
     } else {
         CK(launch_link(b, p, cfg, s));
         CK(rec("link"));

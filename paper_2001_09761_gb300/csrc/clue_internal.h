@@ -207,6 +207,7 @@ cudaError_t launch_nh_rest(const Buffers &b, const Params &p, const LaunchCfg &c
 cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s,
                              int *launches);
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
+bool seed_codes_separate(const Buffers &b);
 cudaError_t launch_seed_codes(const Buffers &b, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_assign(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_expand(const Buffers &b, const LaunchCfg &c, cudaStream_t s);  // all levels

@@ -5,16 +5,6 @@
 
 namespace clue {
 
-cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c,
-                             cudaStream_t s, int *launches) {
-    if (p.chase)
-        return exclusive_scan<int32_t>(LoadSeedWord{b.sbits}, b.N / 32 + 1, b.sword,
-                                       (int32_t *)b.scan_partials, c.grid_cap, s, launches);
-    return exclusive_scan<unsigned long long>(LoadPacked{b.code, b.fcount}, b.N, b.hs,
-                                              (unsigned long long *)b.scan_partials, c.grid_cap,
-                                              s, launches);
-}
-
 __global__ void __launch_bounds__(256) k_link(Buffers b, Params p) { link_stage(b, p); }
 
 cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, cudaStream_t s) {
@@ -29,12 +19,10 @@ cudaError_t launch_link(const Buffers &b, const Params &p, const LaunchCfg &c, c
 // two more scattered loads (the rank's word and bits) per hit.  A warp loads
 // 32 words of the bitmap and their prefixes at once (coalesced), then takes
 // its non-empty words one at a time, a lane per bit (coalesced code stores).
-__global__ void __launch_bounds__(256) k_seed_codes(Buffers b) {
+__device__ __forceinline__ void seed_codes_pass(const Buffers &b, int64_t warp, int64_t nwarps) {
     const int64_t nw = b.N / 32 + 1;  // the words the seed scan covers
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned below = lanemask_lt(), me = 1u << lane_id();
-    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < nw;
-         w0 += nwarps * 32) {
+    for (int64_t w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
         const int64_t wl = w0 + lane_id();
         const unsigned mine = wl < nw ? b.sbits[wl] : 0u;
         const int rmine = wl < nw ? b.sword[wl] : 0;
@@ -47,6 +35,39 @@ __global__ void __launch_bounds__(256) k_seed_codes(Buffers b) {
             if (bits & me) b.code[(w0 + j) * 32 + lane_id()] = CODE_SEED - (r + __popc(bits & below));
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_seed_codes(Buffers b) {
+    seed_codes_pass(b, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                    ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+// A seed bitmap short enough for a one-CTA scan: the scan and the seed codes
+// in one kernel (one launch less for a small run).
+__global__ void __launch_bounds__(SCAN_SINGLE_THREADS) k_seed_scan_single(Buffers b) {
+    scan_single_stage<int32_t, LoadSeedWord>(LoadSeedWord{b.sbits}, b.N / 32 + 1, b.sword);
+    __syncthreads();  // the CTA's own prefix stores are visible to it
+    seed_codes_pass(b, threadIdx.x >> 5, SCAN_SINGLE_THREADS / 32);
+}
+
+// Chase mode: the seed-word scan, and with it the seed codes when the scan
+// runs in one CTA (seed_codes_separate then says no separate launch is due).
+bool seed_codes_separate(const Buffers &b) { return !scan_is_single(b.N / 32 + 1); }
+
+cudaError_t launch_scan_hits(const Buffers &b, const Params &p, const LaunchCfg &c,
+                             cudaStream_t s, int *launches) {
+    if (p.chase) {
+        if (!seed_codes_separate(b)) {
+            k_seed_scan_single<<<1, SCAN_SINGLE_THREADS, 0, s>>>(b);
+            if (launches) *launches += 1;
+            return cudaGetLastError();
+        }
+        return exclusive_scan<int32_t>(LoadSeedWord{b.sbits}, b.N / 32 + 1, b.sword,
+                                       (int32_t *)b.scan_partials, c.grid_cap, s, launches);
+    }
+    return exclusive_scan<unsigned long long>(LoadPacked{b.code, b.fcount}, b.N, b.hs,
+                                              (unsigned long long *)b.scan_partials, c.grid_cap,
+                                              s, launches);
 }
 
 cudaError_t launch_seed_codes(const Buffers &b, const LaunchCfg &c, cudaStream_t s) {

@@ -127,7 +127,7 @@ constexpr int SCAN_SINGLE_THREADS = 1024;
 constexpr int64_t SCAN_SINGLE_TILE = (int64_t)SCAN_SINGLE_THREADS * SCAN_ITEMS;
 
 template <typename T, typename Load>
-__global__ void __launch_bounds__(SCAN_SINGLE_THREADS) k_scan_single(Load ld, int64_t n, T *out) {
+__device__ __forceinline__ void scan_single_stage(const Load &ld, int64_t n, T *out) {
     static_assert(SCAN_SINGLE_THREADS == 32 * 32, "one warp scans the warps' totals");
     __shared__ T wsum[32];
     __shared__ T wtotal;
@@ -167,7 +167,17 @@ __global__ void __launch_bounds__(SCAN_SINGLE_THREADS) k_scan_single(Load ld, in
     if (threadIdx.x == 0) out[n] = carry;
 }
 
+template <typename T, typename Load>
+__global__ void __launch_bounds__(SCAN_SINGLE_THREADS) k_scan_single(Load ld, int64_t n, T *out) {
+    scan_single_stage<T, Load>(ld, n, out);
+}
+
 constexpr int64_t SCAN_SINGLE_MAX_TILES = 4;
+
+// Whether a scan of n elements runs in one CTA (k_scan_single).
+__host__ __device__ constexpr bool scan_is_single(int64_t n) {
+    return (n + SCAN_TILE - 1) / SCAN_TILE <= SCAN_SINGLE_MAX_TILES;
+}
 
 // Exclusive scan of ld(0..n-1) into out[0..n-1], out[n] = total.
 // `partials` must hold scan_partials_needed(n) elements of T.
@@ -175,7 +185,7 @@ template <typename T, typename Load>
 cudaError_t exclusive_scan(Load ld, int64_t n, T *out, T *partials, int grid_cap, cudaStream_t s,
                            int *launches) {
     const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    if (ntiles <= SCAN_SINGLE_MAX_TILES) {
+    if (scan_is_single(n)) {
         k_scan_single<T, Load><<<1, SCAN_SINGLE_THREADS, 0, s>>>(ld, n, out);
         if (launches) *launches += 1;
         return cudaGetLastError();

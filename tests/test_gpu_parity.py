@@ -700,8 +700,7 @@ def test_autotune_keeps_results(clue_mod):
 
 def test_stage_times_and_launch_count(clue_mod):
     ev = gen.make_event(100_000, 100, 3, "blobs")
-    for expand, last in ((0, {"expand_level", "complete", "jump"}),
-                         (1, {"seed_codes", "assign", "jump"})):
+    for expand, last in ((0, {"expand_level", "complete", "jump"}), (1, {"assign", "jump"})):
         cl = _cl(clue_mod, gen.EXTENT, 100, expand=expand)
         cl.set_profiling(True)
         cl.run(ev.x, ev.y, ev.layer, ev.energy, gen.PARAMS_BLOBS)
@@ -711,8 +710,9 @@ def test_stage_times_and_launch_count(clue_mod):
         kt = cl.kernel_times()
         assert {"fill_cells", "density", "nh_rest"} | last <= set(kt)
         # two-level grid fill with a one-CTA segment scan (4); chase: one-CTA
-        # seed-rank scan and the seed codes; both end with the pointer-jumping kernel
-        assert cl.launch_count() == (4 + 20 if expand == 0 else 10)
+        # seed-rank scan that also writes the seed codes; both end with the
+        # pointer-jumping kernel
+        assert cl.launch_count() == (4 + 20 if expand == 0 else 9)
 
 
 def test_paper_parameter_workload(clue_mod):
