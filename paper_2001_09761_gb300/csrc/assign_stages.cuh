@@ -144,16 +144,19 @@ __device__ __forceinline__ void jump_rounds(const Buffers &b, int np, int rounds
 // Chase mode (CLUE_EXPAND_CHASE): ids with no follower lists.  Every hit walks
 // its chain of codes (a follower's code is its nearest-higher) up to the first
 // hit that is not a follower, and takes that hit's id: a seed's rank among its
-// event's seeds (k_seed_codes has put the seed's rank among the batch's seeds
-// in its code), or -1 at an outlier or at a hit with no nearest-higher -- the closed form "a follower inherits the id of its
-// nearest-higher" of Algorithm 3's expansion.  A seed's chain is the seed
+// event's seeds (the seed-word scan, or k_seed_codes after it, has put the
+// seed's rank among the batch's seeds in its code), or -1 at an outlier or at
+// a hit with no nearest-higher -- the closed form "a follower inherits the id
+// of its nearest-higher" of Algorithm 3's expansion.  A seed's chain is the seed
 // itself.  Chains are finite because rho rises strictly along them.  The walk
 // takes at most min(CHASE_STEPS, walk limit) steps; a hit whose chain is
 // longer stays pending and is finished by pointer jumping (jump_rounds, the
 // next kernel) with the rest of the limit, so no chain costs more than
 // O(log depth) rounds.
 __device__ __forceinline__ void assign_stage(const Buffers &b, const Params &p) {
-    constexpr int U = 4;  // hits in flight per thread: their walks overlap
+    // hits in flight per thread: their walks overlap, but a warp walks until
+    // the longest of its 32 U chains ends (two measured best)
+    constexpr int U = 2;
     const int kmax = min(CHASE_STEPS, p.walk_limit);
     for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
         const Tile tl = b.tiles[t];

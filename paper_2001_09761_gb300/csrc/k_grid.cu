@@ -34,15 +34,17 @@ cudaError_t launch_fill_canon(const Buffers &b, const Params &p, const LaunchCfg
     return cudaGetLastError();
 }
 
-// The two tile-wise stages run one CTA per tile: a tile's steps are separated
-// by barriers, and many resident CTAs hide each other's latencies.
 __global__ void __launch_bounds__(FILL_THREADS) k_fill_layers(Buffers b, Params p) {
     fill_layers_stage(b, p);
 }
 
-cudaError_t launch_fill_layers(const Buffers &b, const Params &p, const LaunchCfg &, cudaStream_t s) {
+// A grid of at most grid_cap CTAs (eight per SM), each taking tiles in turn:
+// a tile's count is short, and CTAs that stay resident save the launch of one
+// CTA per tile.
+cudaError_t launch_fill_layers(const Buffers &b, const Params &p, const LaunchCfg &c,
+                               cudaStream_t s) {
     if (p.L < 1 || p.L > SEG_MAX_LAYERS) return cudaErrorInvalidValue;
-    const int grid = b.ntiles;
+    const int grid = b.ntiles < c.grid_cap ? b.ntiles : c.grid_cap;
     k_fill_layers<<<grid > 0 ? grid : 1, FILL_THREADS, (size_t)p.L * 4, s>>>(b, p);
     return cudaGetLastError();
 }
@@ -52,6 +54,8 @@ cudaError_t launch_scan_segs(const Buffers &b, const LaunchCfg &c, cudaStream_t 
                                    (int32_t *)b.scan_partials, c.grid_cap, s, launches);
 }
 
+// The placement runs one CTA per tile: a tile's steps are separated by
+// barriers, and many resident CTAs hide each other's latencies.
 __global__ void __launch_bounds__(FILL_THREADS, 6) k_fill_place(Buffers b, Params p) {
     fill_place_stage(b, p);
 }
