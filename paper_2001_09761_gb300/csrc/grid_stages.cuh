@@ -420,7 +420,9 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
         const FixedW fw = fixed_weights(b.wexp + 2 * e, p.chi);
         if (small && n > 0 && threadIdx.x == 0) prefetch_l2_bulk(b.rec + s0, (unsigned)n * 16u);
         const unsigned short *cell = b.cell16 + s0;
-        smem_zero4(s_cell, n4);
+        // zero the wider (32-bit) counters' extent: it covers the 16-bit ones
+        // too, and needs only the event's grid, not the segment's size
+        smem_zero4(s_cell, (nbxy + 3) / 4);
         __syncthreads();
         for (int k0 = threadIdx.x; k0 < n; k0 += C * SEG_THREADS) {
             unsigned c[C];

@@ -113,6 +113,24 @@ def test_parity_forced_density_kernels(clue_mod, kind, n, L, params, seed, ext, 
     assert_parity(_gpu_all(cl, ev, params), oracle.run_event(ev, params, L, extent=ext))
 
 
+@pytest.mark.parametrize("kind,n,L,seed,ext", [
+    ("irregular", 50_000, 5, 7, gen.EXTENT),
+    ("blobs", 20_000, 2, 8, (-40.0, 40.0, -40.0, 40.0)),
+    ("uniform", 30_000, 1, 9, (-60.0, 60.0, -60.0, 60.0)),
+])
+def test_fused_kernel_at_the_smallest_staging(clue_mod, kind, n, L, seed, ext):
+    """The fused kernel forced at the smallest staging capacity (1792 records),
+    so that tiles take every path it has: the halo's densities from the
+    widened staging where their windows fit it, by walks in global memory
+    where they do not, and the list-driven nh kernel for bands past it."""
+    ev = gen.make_event(n, L, seed, kind, extent=ext)
+    params = gen.PARAMS_IRREGULAR if kind == "irregular" else gen.PARAMS_BLOBS
+    cl = _cl(clue_mod, ext, L, density=clue_mod.CLUE_DENSITY_FUSED)
+    cl.tuning = cl.tuning.replace("band 0", "band 1792")
+    assert "band 1792" in cl.tuning
+    assert_parity(_gpu_all(cl, ev, params), oracle.run_event(ev, params, L, extent=ext))
+
+
 def test_parity_scaling_event_full_size(clue_mod):
     """100 layers x 10k hits (1M hits), the largest single event of the
     scaling sweep, compared in full."""
