@@ -69,6 +69,11 @@ struct Plan {
     int64_t nseg = 0;   // events x layers when the two-level sort applies, else 0
     int64_t ntb = 0;    // tiles x layers (the two-level sort's run table), else 0
     int max_cells = 0;  // most cells in one layer of the batch
+    // the cell sort's event order (two-level sort): the events its small
+    // build takes first (n_small of them, small_cells the most cells in one
+    // of their layers), then the others
+    std::vector<int32_t> seg_ev;
+    int n_small = 0, small_cells = 0;
 };
 
 uint64_t fnv(uint64_t h, const void *p, size_t n) {
@@ -231,6 +236,22 @@ int build_plan(clue_ctx *ctx, const int64_t *offsets, int32_t E, float dc, Plan 
                      ntb <= 4 * plan.N + (1 << 22);
     plan.nseg = seg ? (int64_t)E * o.max_layers : 0;
     plan.ntb = seg ? ntb : 0;
+    plan.seg_ev.clear();
+    plan.n_small = plan.small_cells = 0;
+    if (seg) {
+        auto small = [&](const EventDesc &d) {
+            return (int64_t)d.nbx * d.nby <= SMALL_SEG_CELLS &&
+                   d.n <= (int64_t)SMALL_SEG_MEAN * o.max_layers;
+        };
+        for (int32_t e = 0; e < E; ++e)
+            if (small(plan.ev[e])) {
+                plan.seg_ev.push_back(e);
+                plan.small_cells = std::max(plan.small_cells, plan.ev[e].nbx * plan.ev[e].nby);
+            }
+        plan.n_small = (int)plan.seg_ev.size();
+        for (int32_t e = 0; e < E; ++e)
+            if (!small(plan.ev[e])) plan.seg_ev.push_back(e);
+    }
     return CLUE_OK;
 }
 
@@ -318,19 +339,28 @@ int ensure_arena(clue_ctx *ctx, size_t need) {
     return CLUE_OK;
 }
 
+// Device tables of a run: the events, the tiles, the cell sort's event order.
 size_t tables_bytes(const Plan &plan) {
-    return align_up(plan.ev.size() * sizeof(EventDesc)) + plan.tiles.size() * sizeof(Tile);
+    return align_up(plan.ev.size() * sizeof(EventDesc)) +
+           align_up(plan.tiles.size() * sizeof(Tile)) + plan.seg_ev.size() * sizeof(int32_t);
 }
 
 void fill_tables(const Plan &plan, char *dst) {
+    const size_t a = align_up(plan.ev.size() * sizeof(EventDesc));
+    const size_t t = align_up(plan.tiles.size() * sizeof(Tile));
     std::memcpy(dst, plan.ev.data(), plan.ev.size() * sizeof(EventDesc));
-    std::memcpy(dst + align_up(plan.ev.size() * sizeof(EventDesc)), plan.tiles.data(),
-                plan.tiles.size() * sizeof(Tile));
+    std::memcpy(dst + a, plan.tiles.data(), plan.tiles.size() * sizeof(Tile));
+    std::memcpy(dst + a + t, plan.seg_ev.data(), plan.seg_ev.size() * sizeof(int32_t));
 }
 
 void point_tables(Buffers &b, const Plan &plan, void *dtables) {
+    const size_t a = align_up(plan.ev.size() * sizeof(EventDesc));
+    const size_t t = align_up(plan.tiles.size() * sizeof(Tile));
     b.events = (const EventDesc *)dtables;
-    b.tiles = (const Tile *)((char *)dtables + align_up(plan.ev.size() * sizeof(EventDesc)));
+    b.tiles = (const Tile *)((char *)dtables + a);
+    b.seg_ev = plan.seg_ev.empty() ? nullptr : (const int32_t *)((char *)dtables + a + t);
+    b.n_small_ev = plan.n_small;
+    b.small_cells = plan.small_cells;
     b.ntiles = (int32_t)plan.tiles.size();
     b.nevents = (int32_t)plan.ev.size();
     b.N = plan.N;
@@ -460,6 +490,7 @@ int enqueue(clue_ctx *ctx, const Buffers &b, const Params &p, const LaunchCfg &c
         CK(rec("fill_place"));
         CK(launch_fill_cells(b, p, b.max_cells, s));
         CK(rec("fill_cells"));
+        if (b.seg_ev && b.n_small_ev > 0 && b.n_small_ev < b.nevents) ++nl;  // both builds
     } else {  // direct sort over all cells
         CK(launch_fill_count(b, p, cfg, s));
         CK(rec("fill_count"));
@@ -577,15 +608,16 @@ uint64_t signature(const clue_ctx *ctx, const Plan &plan, const Buffers &b, cons
 
 // The shape of a run's launch sequence: expansion mode, form of the grid
 // fill, the density kernels' build (CTAs above 256 threads use another
-// kernel, which an executable graph's update cannot swap in) and, for each
-// prefix sum, whether it runs in one CTA (at most SCAN_SINGLE_MAX_TILES
-// tiles).
+// kernel, which an executable graph's update cannot swap in), which builds
+// of the cell sort run and, for each prefix sum, whether it runs in one CTA
+// (at most SCAN_SINGLE_MAX_TILES tiles).
 int pipeline_shape(const Buffers &b, const Params &p, const LaunchCfg &cfg) {
     auto one = [](int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE <= SCAN_SINGLE_MAX_TILES; };
     const int64_t first = b.nseg ? b.ntb : b.C;           // run table / cells
     const int64_t second = p.chase ? b.N / 32 + 1 : b.N;  // seed words / packed scan
+    const bool small = b.seg_ev && b.n_small_ev > 0, large = !b.seg_ev || b.n_small_ev < b.nevents;
     return (p.chase ? 1 : 0) | (one(first) ? 2 : 0) | (one(second) ? 4 : 0) | (b.nseg ? 8 : 0) |
-           (cfg.block_density > 256 ? 16 : 0);
+           (cfg.block_density > 256 ? 16 : 0) | (small ? 32 : 0) | (large ? 64 : 0);
 }
 
 // Queue a run whose exact signature has no cached graph: capture it, and

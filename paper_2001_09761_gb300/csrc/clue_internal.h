@@ -15,6 +15,10 @@ constexpr int TILE = 1024;
 // and cells per layer (counted in one CTA's shared memory).
 constexpr int SEG_MAX_LAYERS = 1024;
 constexpr int SEG_MAX_CELLS = 16384;
+// Events the cell sort's small build (128-thread CTAs) takes: at most
+// SMALL_SEG_CELLS cells per layer and SMALL_SEG_MEAN hits per layer on average.
+constexpr int SMALL_SEG_CELLS = 4096;
+constexpr int SMALL_SEG_MEAN = 1024;
 
 // Candidates the density kernels stage per tile (16 bytes each): a launch's
 // capacity (Params::band_cap) lies in [BAND_CAP_MIN, BAND_CAP_MAX], chosen per
@@ -138,6 +142,10 @@ struct Buffers {
                              //     sort; aliases key)
     int64_t nseg;        // events x layers, or 0: the direct sort
     int32_t max_cells;   // most cells in one layer (the cell sort's shared memory)
+    const int32_t *seg_ev;  // the cell sort's event order: its small build's events
+                            //     first (n_small_ev of them), or null: all, in order
+    int32_t n_small_ev;
+    int32_t small_cells;    // most cells in one layer of those events
     int32_t *tmp;        // [N] the sorted ids (sid)
     float4 *sp;          // [N] hits sorted by (event, layer, cell): x, y, w, id (int
                          //     bits), or for an event on the flat kernel's fixed point

@@ -103,8 +103,12 @@ __device__ __forceinline__ void fill_canon_stage(const Buffers &b, const Params 
 constexpr int FILL_THREADS = 256;      // block of the tile-wise stages (TILE / 4)
 constexpr int SEG_THREADS = 512;       // block of the per-segment stage
 constexpr int SEG_SMEM_HITS = 16384;   // segments up to this size are permuted in shared memory
+// The per-segment stage's small build (events chosen by the host, see
+// SMALL_SEG_CELLS; a segment longer than SMALL_SEG_HITS is still sorted
+// right, through global memory).
+constexpr int SMALL_SEG_THREADS = 128;
+constexpr int SMALL_SEG_HITS = 4096;
 static_assert(TILE % FILL_THREADS == 0, "tile / block");
-static_assert(SEG_SMEM_HITS <= 65536, "16-bit indices");
 
 // Where the run table holds (event e, layer l, tile t of e).
 // Layer l == L addresses the next event's block (the table's end for the
@@ -380,42 +384,55 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) 
 // prefetched into L2 (they are read once more, in sorted order, at the end).
 // Its hits are counted per cell in shared memory (cells from `cell16`), the
 // counts scanned and the layer's cell offsets written.  A segment of at most
-// SEG_SMEM_HITS hits keeps 16-bit counters, two to a word (its offsets stay
+// PERM_HITS hits keeps 16-bit counters, two to a word (its offsets stay
 // below 2^16), and is then permuted in shared memory: a second pass over its
 // cells (just read, so in L2) takes each hit's slot with a shared atomic on
 // its cell's running offset and stores the hit's 16-bit index there; the
 // records are then written in slot order, a gather from L2 and coalesced
 // stores.  A longer segment counts in 32-bit words, keeps the first pass's
 // ranks in `perm` and writes each record at its cell's offset plus its rank.
-// Loads are issued in batches ahead of the atomics and stores that use them;
-// the kernel keeps to 42 registers so that three CTAs share an SM (the
-// shared memory of a 16k-cell layer allows three).  The last segment also
-// writes the end offset cell_start[C].  Needs SEG_THREADS threads and
-// fill_cells_smem(nbx * nby) bytes of dynamic shared memory.
+// Loads are issued in batches ahead of the atomics and stores that use them.
+// The last segment also writes the end offset cell_start[C].  Two builds: 512
+// threads and SEG_SMEM_HITS-hit permutations (42 registers: three CTAs per
+// SM, which the shared memory of a 16k-cell layer allows), and 128 threads
+// and SMALL_SEG_HITS for the run's events of few hits per layer and few
+// cells (a dozen CTAs per SM, so that their many short segments overlap).
+// Needs fill_cells_smem<PERM_HITS>(cells_cap) bytes of dynamic shared memory.
+template <int PERM_HITS>
 __host__ __device__ constexpr int fill_cells_smem(int max_cells) {
-    return (max_cells + 3) / 4 * 16 > (max_cells + 7) / 8 * 16 + SEG_SMEM_HITS * 2
+    return (max_cells + 3) / 4 * 16 > (max_cells + 7) / 8 * 16 + PERM_HITS * 2
                ? (max_cells + 3) / 4 * 16
-               : (max_cells + 7) / 8 * 16 + SEG_SMEM_HITS * 2;
+               : (max_cells + 7) / 8 * 16 + PERM_HITS * 2;
 }
 
-__device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params &p) {
+// THREADS per CTA; segments of at most PERM_HITS hits are permuted in shared
+// memory; the CTAs take the segments of events seg_ev[ev0 .. ev0 + n_ev)
+// (all events in order when the run has no such list), layer by layer, and
+// cells_cap bounds their layers' cells (the shared memory's layout).
+template <int THREADS, int PERM_HITS>
+__device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params &p, int ev0,
+                                                 int n_ev, int cells_cap) {
+    static_assert(PERM_HITS <= 65536, "16-bit indices and offsets");
     extern __shared__ int4 s_cell4[];
     __shared__ int ws[32];
     int *s_cell = reinterpret_cast<int *>(s_cell4);             // 32-bit counters (long segments)
     unsigned *s_c16 = reinterpret_cast<unsigned *>(s_cell4);    // 16-bit counters (short ones)
-    unsigned short *s_perm = (unsigned short *)(s_cell4 + (b.max_cells + 7) / 8);
+    unsigned short *s_perm = (unsigned short *)(s_cell4 + (cells_cap + 7) / 8);
     constexpr int C = 8;  // cells loaded per batch
     constexpr int G = 2;  // gathers in flight per thread
-    for (int64_t sg = blockIdx.x; sg < b.nseg; sg += gridDim.x) {
-        const int e = (int)(sg / p.L);
-        const int l = (int)(sg - (int64_t)e * p.L);
+    const int64_t nseg = (int64_t)n_ev * p.L;
+    for (int64_t i = blockIdx.x; i < nseg; i += gridDim.x) {
+        const int at = ev0 + (int)(i / p.L);
+        const int e = b.seg_ev ? b.seg_ev[at] : at;
+        const int l = (int)(i % p.L);
+        const int64_t sg = (int64_t)e * p.L + l;  // the segment's place in the run
         const EventDesc ev = b.events[e];
         const int nbxy = ev.nbx * ev.nby;
         const int64_t cbase = ev.cell_off + (int64_t)l * nbxy;
         // the segment runs from its first tile's run to the next segment's
         const int s0 = b.tbase[run_index(ev, p.L, l, ev.tile0)];
         const int n = b.tbase[run_index(ev, p.L, l + 1, ev.tile0)] - s0;
-        const bool small = n <= SEG_SMEM_HITS;  // uniform over the CTA
+        const bool small = n <= PERM_HITS;  // uniform over the CTA
         const int n4 = small ? (nbxy + 7) / 8 : (nbxy + 3) / 4;
         const FixedW fw = fixed_weights(b.wexp + 2 * e, p.chi);
         if (small && n > 0 && threadIdx.x == 0) prefetch_l2_bulk(b.rec + s0, (unsigned)n * 16u);
@@ -424,11 +441,11 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
         // too, and needs only the event's grid, not the segment's size
         smem_zero4(s_cell, (nbxy + 3) / 4);
         __syncthreads();
-        for (int k0 = threadIdx.x; k0 < n; k0 += C * SEG_THREADS) {
+        for (int k0 = threadIdx.x; k0 < n; k0 += C * THREADS) {
             unsigned c[C];
 #pragma unroll
             for (int u = 0; u < C; ++u) {
-                const int k = k0 + u * SEG_THREADS;
+                const int k = k0 + u * THREADS;
                 c[u] = k < n ? cell[k] : 0xffffu;
             }
 #pragma unroll
@@ -438,34 +455,34 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
                     inc16(s_c16, c[u]);
                 } else {
                     const int rk = atomicAdd(&s_cell[c[u]], 1);
-                    b.perm[s0 + k0 + u * SEG_THREADS] = rk;
+                    b.perm[s0 + k0 + u * THREADS] = rk;
                 }
             }
         }
         __syncthreads();
         if (small) {
             smem_excl_scan16(s_c16, n4, ws);
-            for (int c = threadIdx.x; c < nbxy; c += SEG_THREADS)
+            for (int c = threadIdx.x; c < nbxy; c += THREADS)
                 b.cell_start[cbase + c] = s0 + get16(s_c16, (unsigned)c);
         } else {
             smem_excl_scan4(s_cell, n4, ws);
-            for (int c = threadIdx.x; c < nbxy; c += SEG_THREADS)
+            for (int c = threadIdx.x; c < nbxy; c += THREADS)
                 b.cell_start[cbase + c] = s0 + s_cell[c];
         }
         if (sg == b.nseg - 1 && threadIdx.x == 0) b.cell_start[b.C] = s0 + n;
         if (small) {
             __syncthreads();  // the offsets are read before they become cursors
-            for (int k0 = threadIdx.x; k0 < n; k0 += C * SEG_THREADS) {
+            for (int k0 = threadIdx.x; k0 < n; k0 += C * THREADS) {
                 unsigned c[C];
 #pragma unroll
                 for (int u = 0; u < C; ++u) {
-                    const int k = k0 + u * SEG_THREADS;
+                    const int k = k0 + u * THREADS;
                     c[u] = k < n ? cell[k] : 0xffffu;
                 }
 #pragma unroll
                 for (int u = 0; u < C; ++u) {
                     if (c[u] == 0xffffu) break;
-                    s_perm[inc16(s_c16, c[u])] = (unsigned short)(k0 + u * SEG_THREADS);
+                    s_perm[inc16(s_c16, c[u])] = (unsigned short)(k0 + u * THREADS);
                 }
             }
             __syncthreads();
@@ -473,14 +490,14 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
             float4 *sp = b.sp + s0;
             int32_t *sid = b.sid + s0;
             int32_t *lay = b.lay_s + s0;
-            for (int q0 = threadIdx.x; q0 < n; q0 += G * SEG_THREADS) {
+            for (int q0 = threadIdx.x; q0 < n; q0 += G * THREADS) {
                 float4 v[G];
 #pragma unroll
                 for (int u = 0; u < G; ++u)
-                    if (q0 + u * SEG_THREADS < n) v[u] = rec[s_perm[q0 + u * SEG_THREADS]];
+                    if (q0 + u * THREADS < n) v[u] = rec[s_perm[q0 + u * THREADS]];
 #pragma unroll
                 for (int u = 0; u < G; ++u) {
-                    const int q = q0 + u * SEG_THREADS;
+                    const int q = q0 + u * THREADS;
                     if (q < n) {
                         sp[q] = sorted_record(v[u], fw);
                         sid[q] = __float_as_int(v[u].w);
@@ -489,13 +506,13 @@ __device__ __forceinline__ void fill_cells_stage(const Buffers &b, const Params 
                 }
             }
         } else {
-            for (int k = threadIdx.x; k < n; k += SEG_THREADS) {
+            for (int k = threadIdx.x; k < n; k += THREADS) {
                 const float4 r = b.rec[s0 + k];
                 const int q = s0 + s_cell[cell[k]] + b.perm[s0 + k];
                 b.sp[q] = sorted_record(r, fw);
                 b.sid[q] = __float_as_int(r.w);
             }
-            for (int k = threadIdx.x; k < n; k += SEG_THREADS) b.lay_s[s0 + k] = l;
+            for (int k = threadIdx.x; k < n; k += THREADS) b.lay_s[s0 + k] = l;
         }
         __syncthreads();  // the shared arrays are reset for the next segment
     }

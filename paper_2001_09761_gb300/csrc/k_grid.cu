@@ -67,22 +67,45 @@ cudaError_t launch_fill_place(const Buffers &b, const Params &p, const LaunchCfg
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(SEG_THREADS, 3) k_fill_cells(Buffers b, Params p) {
-    fill_cells_stage(b, p);
+__global__ void __launch_bounds__(SEG_THREADS, 3)
+    k_fill_cells(Buffers b, Params p, int ev0, int n_ev, int cells_cap) {
+    fill_cells_stage<SEG_THREADS, SEG_SMEM_HITS>(b, p, ev0, n_ev, cells_cap);
 }
 
+__global__ void __launch_bounds__(SMALL_SEG_THREADS, 12)
+    k_fill_cells_small(Buffers b, Params p, int ev0, int n_ev, int cells_cap) {
+    fill_cells_stage<SMALL_SEG_THREADS, SMALL_SEG_HITS>(b, p, ev0, n_ev, cells_cap);
+}
 
 cudaError_t fill_prepare() {
-    return cudaFuncSetAttribute(k_fill_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                fill_cells_smem(SEG_MAX_CELLS));
+    cudaError_t e = cudaFuncSetAttribute(k_fill_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         fill_cells_smem<SEG_SMEM_HITS>(SEG_MAX_CELLS));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fill_cells_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                fill_cells_smem<SMALL_SEG_HITS>(SMALL_SEG_CELLS));
 }
 
-// One CTA per segment (a grid-stride loop past 2^30 segments).
+// One CTA per segment (a grid-stride loop past 2^30 segments): the small
+// build over the run's first n_small_ev events of seg_ev, the large one over
+// the rest (or over all events when the run has no list).
 cudaError_t launch_fill_cells(const Buffers &b, const Params &p, int max_cells, cudaStream_t s) {
     if (max_cells < 1 || max_cells > SEG_MAX_CELLS || max_cells != b.max_cells || b.nseg < 1)
         return cudaErrorInvalidValue;
-    const int64_t grid = b.nseg < (1 << 30) ? b.nseg : (1 << 30);
-    k_fill_cells<<<(unsigned)grid, SEG_THREADS, (size_t)fill_cells_smem(max_cells), s>>>(b, p);
+    const int n_small = b.seg_ev ? b.n_small_ev : 0;
+    if (n_small < 0 || n_small > b.nevents || b.small_cells > SMALL_SEG_CELLS) return cudaErrorInvalidValue;
+    const int64_t cap = 1 << 30;
+    if (n_small > 0) {
+        const int64_t nseg = (int64_t)n_small * p.L;
+        k_fill_cells_small<<<(unsigned)(nseg < cap ? nseg : cap), SMALL_SEG_THREADS,
+                             (size_t)fill_cells_smem<SMALL_SEG_HITS>(b.small_cells), s>>>(
+            b, p, 0, n_small, b.small_cells);
+    }
+    if (n_small < b.nevents) {
+        const int64_t nseg = (int64_t)(b.nevents - n_small) * p.L;
+        k_fill_cells<<<(unsigned)(nseg < cap ? nseg : cap), SEG_THREADS,
+                       (size_t)fill_cells_smem<SEG_SMEM_HITS>(max_cells), s>>>(
+            b, p, n_small, b.nevents - n_small, max_cells);
+    }
     return cudaGetLastError();
 }
 
