@@ -534,6 +534,31 @@ def test_grid_fill_forms(clue_mod, form):
     assert ("fill_count" in names) == direct and ("fill_cells" in names) == (not direct)
 
 
+def test_cell_sort_builds_and_their_long_segments(clue_mod):
+    """The cell sort's two builds in one batch, each meeting a segment longer
+    than it permutes in shared memory: an event of few hits per layer on
+    average (the 128-thread build) whose hits all sit in one layer (a
+    30000-hit segment, past that build's 4096), beside events of many hits
+    per layer (the 512-thread build), one with a 20000-hit layer."""
+    ext = (-60.0, 60.0, -60.0, 60.0)
+    L = 40
+    crowded = gen.make_event(30_000, 1, 81, "blobs", extent=ext)  # layer 0 only
+    sparse = gen.make_event(8_000, L, 82, "blobs", extent=ext)
+    dense = gen.make_event(60_000, 3, 83, "blobs", extent=ext)     # ~20000 hits per layer
+    evs = [crowded, sparse, dense]
+    x, y, l, e, offs = gen.concat(evs)
+    cl = _cl(clue_mod, ext, L, bin_size=4.0)  # 30 x 30 cells per layer: the small build's limit
+    cl.set_profiling(True)
+    cid, seed = cl.run_batch(x, y, l, e, offs, gen.PARAMS_BLOBS)
+    cl.sync()
+    cid, seed = cid.cpu().numpy(), seed.cpu().numpy()
+    assert "fill_cells" in cl.kernel_times()
+    for i, ev in enumerate(evs):
+        ref = oracle.run_event(ev, gen.PARAMS_BLOBS, L, extent=ext)
+        assert np.array_equal(cid[offs[i]:offs[i + 1]], ref["cluster_id"]), i
+        assert np.array_equal(seed[offs[i]:offs[i + 1]], ref["is_seed"]), i
+
+
 @pytest.mark.parametrize("expand", [0, 1], ids=["frontier", "chase"])
 def test_wide_tree_one_node_with_many_followers(clue_mod, expand):
     """2000 hits on a circle of radius 3 around one heavy hit.  They are
