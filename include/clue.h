@@ -71,9 +71,11 @@ typedef struct clue_opts {
     float bin_size;      /* grid bin size (cm); 0 = from the tuning table */
     int32_t block_size;  /* threads per block of the density kernels (32..256, a
                             multiple of 32); 0 = from the tuning table, whose
-                            default (block 0) picks 128 for runs of at least
-                            8 tiles of 1024 hits per SM, 256 for at least one
-                            tile per SM and 1024 below */
+                            block line the autotuner sets from 128, 256 and
+                            512; its default (block 0) picks, per run, 256
+                            for runs of at least one tile per SM (512 when the
+                            run's staging leaves room for only two CTAs of
+                            256 per SM) and 1024 for runs of fewer tiles */
     int32_t use_graphs;  /* 1 = capture a repeated call into a CUDA graph and replay it */
     void *stream;        /* cudaStream_t to queue work on; NULL = context-owned stream */
     int32_t expand;      /* how ids reach the followers (identical results):
