@@ -27,7 +27,7 @@ constexpr int SMALL_SEG_MEAN = 1024;
 constexpr int BAND_CAP_MIN = 1792;
 constexpr int BAND_CAP_MAX = 6144;
 // Static shared memory of a density CTA (its per-tile state), besides the band.
-constexpr int DENSITY_SMEM_FIXED = 18752;
+constexpr int DENSITY_SMEM_FIXED = 18736;
 
 // Cluster id of a follower whose id has not been passed down yet (frontier
 // expansion).

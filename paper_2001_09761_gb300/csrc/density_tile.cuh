@@ -50,7 +50,6 @@ struct DensityShared {
     unsigned short perm[TILE];         // the tile's hits by descending window population
     int hist[DT_BUCKETS];
     int lo, hi, rows;                  // the band [lo, hi) (relative) and the most rows
-    unsigned long long tsum;           // candidates over the tile's windows
     int lo2, hi2, hrows;               // the fused form's staging: the band and the halo
                                        // hits' own density windows, their most rows
     int next[2];                       // the sorted form's work counters (rho, nh)
@@ -85,12 +84,31 @@ __device__ __forceinline__ bool stage_band(const Buffers &b, const float4 *src, 
     return ok;
 }
 
+// Add one to counter cnt[key] for every lane of the warp (key < 0: none) and
+// return the lane's slot: the counter's old value plus the lane's rank among
+// the lanes of equal key.  Lanes of equal key share one shared-memory atomic
+// (neighbouring hits often fall in the same class).  All 32 lanes call it.
+__device__ __forceinline__ int warp_class_add(int *cnt, int key) {
+    const unsigned peers = __match_any_sync(FULL_MASK, key);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane_id() == leader && key >= 0) base = atomicAdd(&cnt[key], __popc(peers));
+    base = __shfl_sync(FULL_MASK, base, leader);
+    return base + __popc(peers & lanemask_lt());
+}
+
+// The work class of a window of T candidates (descending T: class 0 first).
+__device__ __forceinline__ int work_class(unsigned T) {
+    return DT_BUCKETS - 1 - (int)min(T, (unsigned)(DT_BUCKETS - 1));
+}
+
 // The tile's windows of radius parameter `dr` into sh.win (rows past DT_ROWS
 // and starts past DT_OUT are flagged through sh.rows / the band, which then
 // disqualify the sorted form), the band and the work histogram.  A thread
 // takes the tile's hits k = threadIdx.x + u * blockDim.x, u < U, and issues
 // each round of loads (records and layers, then every window row's bounds)
-// for all of them before it waits on any.
+// for all of them before it waits on any.  Cell indices are 32-bit (a run
+// has at most 2^31 - 2 cells).  The loop runs alike in all lanes of a warp.
 template <int U>
 __device__ __forceinline__ void tile_windows(const Buffers &b, const Tile &tl,
                                              const EventDesc &ev, float dr,
@@ -100,15 +118,14 @@ __device__ __forceinline__ void tile_windows(const Buffers &b, const Tile &tl,
         sh.lo = INT_MAX;
         sh.hi = INT_MIN;
         sh.rows = 0;
-        sh.tsum = 0ull;
         sh.next[0] = 0;
         sh.next[1] = 0;
     }
     __syncthreads();
-    const int64_t nbxy = (int64_t)ev.nbx * ev.nby;
+    const int32_t *cs = b.cell_start + ev.cell_off;  // the event's cells
+    const int nbx = ev.nbx, nbxy = ev.nbx * ev.nby;
     int lo = INT_MAX, hi = INT_MIN, rows = 0;
-    unsigned long long tsum = 0ull;
-    for (int k0 = threadIdx.x; k0 < tl.len; k0 += U * blockDim.x) {
+    for (int k0 = threadIdx.x; k0 - lane_id() < tl.len; k0 += U * blockDim.x) {
         float4 me[U];
         int lay[U];
 #pragma unroll
@@ -119,57 +136,56 @@ __device__ __forceinline__ void tile_windows(const Buffers &b, const Tile &tl,
             lay[u] = b.lay_s[q];
         }
         Window w[U];
-        int64_t row0[U];
+        int row0[U];
         int a[U][DT_ROWS], e[U][DT_ROWS];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             w[u] = window_of(me[u].x, me[u].y, dr, ev);
-            row0[u] = ev.cell_off + (int64_t)lay[u] * nbxy + (int64_t)w[u].ly * ev.nbx;
+            row0[u] = lay[u] * nbxy + w[u].ly * nbx;
 #pragma unroll
             for (int r = 0; r < DT_ROWS; ++r) {
                 const bool in = w[u].ly + r <= w[u].hy;
-                const int64_t row = row0[u] + (in ? (int64_t)r * ev.nbx : 0);
-                a[u][r] = in ? b.cell_start[row + w[u].lx] : 0;
-                e[u][r] = in ? b.cell_start[row + w[u].hx + 1] : 0;
+                const int row = row0[u] + (in ? r * nbx : 0);
+                a[u][r] = in ? cs[row + w[u].lx] : 0;
+                e[u][r] = in ? cs[row + w[u].hx + 1] : 0;
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int k = k0 + u * blockDim.x;
-            if (k >= tl.len) continue;
-            const int nr = w[u].hy - w[u].ly + 1;
-            unsigned T = 0;
-            int last = e[u][0];
+            int cls = -1;
+            if (k < tl.len) {
+                const int nr = w[u].hy - w[u].ly + 1;
+                unsigned T = 0;
+                int last = e[u][0];
 #pragma unroll
-            for (int r = 0; r < DT_ROWS; ++r) T += (unsigned)(e[u][r] - a[u][r]);
-            for (int r = DT_ROWS; r < nr; ++r) {  // rows the sorted form does not take
-                const int64_t row = row0[u] + (int64_t)r * ev.nbx;
-                const int u0 = b.cell_start[row + w[u].lx];
-                last = b.cell_start[row + w[u].hx + 1];
-                T += (unsigned)(last - u0);
+                for (int r = 0; r < DT_ROWS; ++r) T += (unsigned)(e[u][r] - a[u][r]);
+                for (int r = DT_ROWS; r < nr; ++r) {  // rows the sorted form does not take
+                    const int row = row0[u] + r * nbx;
+                    const int u0 = cs[row + w[u].lx];
+                    last = cs[row + w[u].hx + 1];
+                    T += (unsigned)(last - u0);
+                }
+                if (nr > 1 && nr <= DT_ROWS) last = nr == 2 ? e[u][1] : e[u][2];
+                lo = min(lo, a[u][0] - tl.start);
+                hi = max(hi, last - tl.start);
+                rows = max(rows, nr);
+                sh.win[k] = make_uint4(pack_row(a[u][0] - tl.start, e[u][0] - a[u][0]),
+                                       pack_row(a[u][1] - tl.start, e[u][1] - a[u][1]),
+                                       pack_row(a[u][2] - tl.start, e[u][2] - a[u][2]),
+                                       min(T, 65535u));
+                cls = work_class(T);
             }
-            if (nr > 1 && nr <= DT_ROWS) last = nr == 2 ? e[u][1] : e[u][2];
-            lo = min(lo, a[u][0] - tl.start);
-            hi = max(hi, last - tl.start);
-            rows = max(rows, nr);
-            tsum += T;
-            sh.win[k] = make_uint4(pack_row(a[u][0] - tl.start, e[u][0] - a[u][0]),
-                                   pack_row(a[u][1] - tl.start, e[u][1] - a[u][1]),
-                                   pack_row(a[u][2] - tl.start, e[u][2] - a[u][2]),
-                                   min(T, 65535u));
-            atomicAdd(&sh.hist[DT_BUCKETS - 1 - min((int)T, DT_BUCKETS - 1)], 1);
+            warp_class_add(sh.hist, cls);
         }
     }
     lo = __reduce_min_sync(FULL_MASK, lo);
     hi = __reduce_max_sync(FULL_MASK, hi);
     rows = __reduce_max_sync(FULL_MASK, rows);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(FULL_MASK, tsum, o);
     if (lane_id() == 0) {
         atomicMin(&sh.lo, lo);
         atomicMax(&sh.hi, hi);
         atomicMax(&sh.rows, rows);
-        atomicAdd(&sh.tsum, tsum);
     }
     __syncthreads();
 }
@@ -192,10 +208,9 @@ __device__ __forceinline__ void tile_sort(const Tile &tl, DensityShared &sh) {
         sh.hist[2 * threadIdx.x + 1] = incl - v1;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-        const int T = (int)sh.win[k].w;
-        const int pos = atomicAdd(&sh.hist[DT_BUCKETS - 1 - min(T, DT_BUCKETS - 1)], 1);
-        sh.perm[pos] = (unsigned short)k;
+    for (int k = threadIdx.x; k - lane_id() < tl.len; k += blockDim.x) {  // alike per warp
+        const int pos = warp_class_add(sh.hist, k < tl.len ? work_class(sh.win[k].w) : -1);
+        if (k < tl.len) sh.perm[pos] = (unsigned short)k;
     }
 }
 
@@ -382,15 +397,16 @@ struct HaloWin {
     __device__ __forceinline__ HaloWin(const Buffers &b, const EventDesc &ev, const Params &p,
                                        const float4 &me, int lay, int tstart) {
         const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
-        const int64_t row0 = ev.cell_off + (int64_t)lay * ev.nbx * ev.nby + (int64_t)w.ly * ev.nbx;
+        const int32_t *cs = b.cell_start + ev.cell_off;  // the event's cells (32-bit indices)
+        const int row0 = lay * (ev.nbx * ev.nby) + w.ly * ev.nbx;
         rows = w.hy - w.ly + 1;
         first = INT_MAX;
         last = INT_MIN;
 #pragma unroll
         for (int r = 0; r < DT_ROWS; ++r) {
             const bool in = r < rows;
-            const int64_t row = row0 + (in ? (int64_t)r * ev.nbx : 0);
-            const int s0 = in ? b.cell_start[row + w.lx] : 0, e = in ? b.cell_start[row + w.hx + 1] : 0;
+            const int row = row0 + (in ? r * ev.nbx : 0);
+            const int s0 = in ? cs[row + w.lx] : 0, e = in ? cs[row + w.hx + 1] : 0;
             a[r] = s0 - tstart;
             l[r] = e - s0;
             if (in) {
