@@ -388,12 +388,26 @@ constexpr int HALO_PER_THREAD = 4;
 // Records a thread restages per round of id loads.
 constexpr int RESTAGE_ILP = 4;
 
+// Halo hits per thread whose windows the sizing pass keeps in registers (as
+// pack_row words) for the density pass; the others' windows are looked up
+// again.  Most tiles have at most two halo hits per thread.
+constexpr int HALO_KEPT = 2;
+
 // A halo hit's density window (radius d_c) as up to DT_ROWS runs of sorted
 // positions (relative to the tile start): its first and last position and
 // its rows (more than DT_ROWS rows: only `rows` is meaningful).
 struct HaloWin {
     int a[DT_ROWS], l[DT_ROWS];
     int first, last, rows;
+    // from the rows as pack_row keeps them (a and l only)
+    __device__ __forceinline__ explicit HaloWin(const unsigned (&pr)[DT_ROWS]) {
+#pragma unroll
+        for (int r = 0; r < DT_ROWS; ++r) {
+            a[r] = row_start(pr[r]);
+            l[r] = row_len(pr[r]);
+        }
+        first = last = rows = 0;
+    }
     __device__ __forceinline__ HaloWin(const Buffers &b, const EventDesc &ev, const Params &p,
                                        const float4 &me, int lay, int tstart) {
         const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
@@ -417,13 +431,14 @@ struct HaloWin {
     }
 };
 
-// rho of a halo hit from the staged band (sorted position tl.start + lo on):
-// the same arithmetic as rho_sorted, over the hit's own d_c window.
+// rho of a halo hit (sorted position q) from the staged band (sorted
+// position tl.start + lo on): the same arithmetic as rho_sorted, over the
+// hit's own d_c window.
 template <int CHI>
 __device__ __forceinline__ float rho_from_band(const Buffers &b, const Params &p,
                                                const EventDesc &ev, const FixedW &fw,
                                                const float4 *band, const HaloWin &hw, int lo,
-                                               const float4 &me, int lay) {
+                                               const float4 &me, int q) {
     const int T = hw.l[0] + hw.l[1] + hw.l[2];
     const int o1 = hw.l[0], o2 = hw.l[0] + hw.l[1];
     const int b0 = hw.a[0] - lo, b1 = hw.a[1] - lo - o1, b2 = hw.a[2] - lo - o2;
@@ -450,7 +465,7 @@ __device__ __forceinline__ float rho_from_band(const Buffers &b, const Params &p
     }
     if (!ok) {
         const Window w = window_of(me.x, me.y, p.rwin_rho, ev);
-        const int64_t plane = ev.cell_off + (int64_t)lay * ev.nbx * ev.nby;
+        const int64_t plane = ev.cell_off + (int64_t)b.lay_s[q] * ev.nbx * ev.nby;
         r = rho_wide<CHI>(b, plane, ev.nbx, w, me.x, me.y, p.dc2, p.chi_inv,
                           CHI == 0 && fw.on ? fw.unit : 0.0f);
     }
@@ -505,13 +520,25 @@ __device__ __forceinline__ bool density_tile(const Buffers &b, const Params &p, 
     }
     __syncthreads();
     const bool halo_fits = n_halo <= HALO_PER_THREAD * (int)blockDim.x;
+    // the first HALO_KEPT halo hits' windows, relative to the tile start (the
+    // wide form's windows lie within the staging, well inside pack_row's range)
+    unsigned kept[HALO_KEPT][DT_ROWS];
+#pragma unroll
+    for (int u = 0; u < HALO_KEPT; ++u)
+#pragma unroll
+        for (int r = 0; r < DT_ROWS; ++r) kept[u][r] = 0u;
     if (halo_fits) {
         int l2 = lo, h2 = hi, rows = 0;
+#pragma unroll
         for (int u = 0; u < HALO_PER_THREAD; ++u) {
             const int i = threadIdx.x + u * (int)blockDim.x;
             if (i >= n_halo) break;
             const int q = tl.start + lo + (i < t0 ? i : i + tl.len);
             const HaloWin hw(b, ev, p, b.sp[q], b.lay_s[q], tl.start);
+            if (u < HALO_KEPT)
+#pragma unroll
+                for (int r = 0; r < DT_ROWS; ++r)
+                    kept[u < HALO_KEPT ? u : 0][r] = pack_row(hw.a[r], hw.l[r]);
             l2 = min(l2, hw.first);
             h2 = max(h2, hw.last);
             rows = max(rows, hw.rows);
@@ -538,8 +565,9 @@ __device__ __forceinline__ bool density_tile(const Buffers &b, const Params &p, 
             if (i < n_halo) {
                 const int q = tl.start + lo + (i < t0 ? i : i + tl.len);
                 const float4 me = band[q - tl.start - base];
-                const HaloWin hw(b, ev, p, me, b.lay_s[q], tl.start);
-                hrho[u] = rho_from_band<CHI>(b, p, ev, fw, band, hw, base, me, b.lay_s[q]);
+                const HaloWin hw = u < HALO_KEPT ? HaloWin(kept[u < HALO_KEPT ? u : 0])
+                                                 : HaloWin(b, ev, p, me, b.lay_s[q], tl.start);
+                hrho[u] = rho_from_band<CHI>(b, p, ev, fw, band, hw, base, me, q);
             }
         }
     }
