@@ -131,6 +131,31 @@ def test_fused_kernel_at_the_smallest_staging(clue_mod, kind, n, L, seed, ext):
     assert_parity(_gpu_all(cl, ev, params), oracle.run_event(ev, params, L, extent=ext))
 
 
+@pytest.mark.parametrize("per_layer,block", [(8000, 128), (12600, 128), (12600, 64),
+                                             (22000, 256)])
+def test_fused_kernel_halo_windows_kept_and_looked_up(clue_mod, per_layer, block):
+    """The fused kernel's halo densities with every number of halo hits per
+    thread.  Bins of 8 cm on the 500 cm extent give 63 bins per row, so a
+    layer of h hits has about h / 63 per grid row, and a 1024-hit tile's band
+    holds about two rows' worth of halo hits (its first and last rows'
+    neighbours): about 250, 400 and 700 for 8000, 12600 and 22000 hits per
+    layer.  So tiles have their halo within the two windows per thread that
+    the kernel keeps from its sizing pass (8000 hits, 128 threads: about half
+    the tiles), past them (the third and fourth window looked up again: 12600
+    hits at 128 threads, 22000 at 256), past the four halo hits a thread
+    takes (12600 hits at 64 threads: the halo's densities by walks in global
+    memory), and a widened band past the staging (some tiles at 22000).  The
+    staging capacity is raised to 2560 records so most widened bands fit."""
+    L = 3
+    ev = gen.make_event(per_layer * L, L, 21, "blobs")
+    cl = _cl(clue_mod, gen.EXTENT, L, bin_size=8.0, block_size=block,
+             density=clue_mod.CLUE_DENSITY_FUSED)
+    cl.tuning = cl.tuning.replace("band 0", "band 2560")
+    assert "band 2560" in cl.tuning
+    assert_parity(_gpu_all(cl, ev, gen.PARAMS_BLOBS),
+                  oracle.run_event(ev, gen.PARAMS_BLOBS, L))
+
+
 def test_parity_scaling_event_full_size(clue_mod):
     """100 layers x 10k hits (1M hits), the largest single event of the
     scaling sweep, compared in full."""
