@@ -389,9 +389,9 @@ constexpr int HALO_PER_THREAD = 4;
 constexpr int RESTAGE_ILP = 4;
 
 // Halo hits per thread whose windows the sizing pass keeps in registers (as
-// pack_row words) for the density pass; the others' windows are looked up
-// again.  Most tiles have at most two halo hits per thread.
-constexpr int HALO_KEPT = 2;
+// pack_row words) for the density pass; a fourth one's window is looked up
+// again.  Most tiles have at most two or three halo hits per thread.
+constexpr int HALO_KEPT = 3;
 
 // A halo hit's density window (radius d_c) as up to DT_ROWS runs of sorted
 // positions (relative to the tile start): its first and last position and

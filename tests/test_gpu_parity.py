@@ -139,13 +139,14 @@ def test_fused_kernel_halo_windows_kept_and_looked_up(clue_mod, per_layer, block
     layer of h hits has about h / 63 per grid row, and a 1024-hit tile's band
     holds about two rows' worth of halo hits (its first and last rows'
     neighbours): about 250, 400 and 700 for 8000, 12600 and 22000 hits per
-    layer.  So tiles have their halo within the two windows per thread that
-    the kernel keeps from its sizing pass (8000 hits, 128 threads: about half
-    the tiles), past them (the third and fourth window looked up again: 12600
-    hits at 128 threads, 22000 at 256), past the four halo hits a thread
-    takes (12600 hits at 64 threads: the halo's densities by walks in global
-    memory), and a widened band past the staging (some tiles at 22000).  The
-    staging capacity is raised to 2560 records so most widened bands fit."""
+    layer.  So tiles have their halo within the three windows per thread that
+    the kernel keeps from its sizing pass (8000 hits at 128 threads, most
+    tiles at 22000 hits and 256 threads), past them (a fourth window looked up
+    again: over half the tiles at 12600 hits and 128 threads, some at 22000),
+    past the four halo hits a thread takes (12600 hits at 64 threads: the
+    halo's densities by walks in global memory), and a widened band past the
+    staging (some tiles at 22000).  The staging capacity is raised to 2560
+    records so most widened bands fit."""
     L = 3
     ev = gen.make_event(per_layer * L, L, 21, "blobs")
     cl = _cl(clue_mod, gen.EXTENT, L, bin_size=8.0, block_size=block,
