@@ -13,7 +13,6 @@ from __future__ import annotations
 
 import json
 import math
-from fractions import Fraction
 from pathlib import Path
 
 import numpy as np

@@ -3,8 +3,6 @@ no data exchange, and only the timing is reduced (max time, summed hits)."""
 import os
 import socket
 
-import numpy as np
-import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
