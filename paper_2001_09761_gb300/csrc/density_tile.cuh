@@ -484,12 +484,12 @@ __device__ __forceinline__ float rho_from_band(const Buffers &b, const Params &p
 // (identical values): the staging is widened to the halo hits' own d_c
 // windows where that fits (their rho then comes from shared memory too), else
 // they walk their windows in global memory; the band restaged in place as
-// (x, y, rho, id); nh and the decision of the tile's hits.  So rho goes straight to nh with no pass over the batch in
-// between.  A tile the sorted form does not take (a band beyond the staging
-// capacity, windows of more rows) or whose halo holds more hits than the tile
-// itself (dense neighbourhoods) gets only its rho here
-// (rho_tile's forms) and joins a list that k_nh_rest finishes after every
-// tile's rho is written.
+// (x, y, rho, id); nh and the decision of the tile's hits.  So rho goes
+// straight to nh with no pass over the batch in between.  A tile the sorted
+// form does not take (a band beyond the staging capacity, windows of more
+// rows) or whose halo holds more hits than the tile itself (dense
+// neighbourhoods) gets only its rho here (rho_tile's forms) and joins a list
+// that k_nh_rest finishes after every tile's rho is written.
 template <int CHI, int U>
 __device__ __forceinline__ bool density_tile(const Buffers &b, const Params &p, int t,
                                              DensityShared &sh, float4 *band, unsigned &parity) {
