@@ -390,7 +390,8 @@ constexpr int RESTAGE_ILP = 4;
 
 // Halo hits per thread whose windows the sizing pass keeps in registers (as
 // pack_row words) for the density pass; a fourth one's window is looked up
-// again.  Most tiles have at most two or three halo hits per thread.
+// again.  At 256 threads a tile of the blob recipe has at most two halo hits
+// per thread; denser grid rows have more.
 constexpr int HALO_KEPT = 3;
 
 // A halo hit's density window (radius d_c) as up to DT_ROWS runs of sorted
